@@ -210,3 +210,53 @@ def dense_matrix(blk, dims, bc=(1, 1, 1, 1)):
             e.reshape(V, 12)[x, k] = 1
             M[:, 12 * x + k] = apply(blk, e, bc).reshape(-1)
     return M
+
+
+def path_at(U, word, coords):
+    """(P, offset) for the sites `coords` ((n, 4) integer array of x, y, z, t): the link product
+    along `word` starting at each site."""
+    T, Z, Y, X = U.shape[:4]
+    sizes = np.array([X, Y, Z, T])
+    n = coords.shape[0]
+    P = np.broadcast_to(np.eye(3, dtype=np.complex128), (n, 3, 3)).copy()
+    pos = coords.astype(np.int64).copy()
+    off = [0, 0, 0, 0]
+
+    def link(mu):
+        w = np.mod(pos, sizes)
+        return U[w[:, 3], w[:, 2], w[:, 1], w[:, 0], mu]
+
+    for s in word:
+        mu = abs(s) - 1
+        if s > 0:
+            P = P @ link(mu)
+            pos[:, mu] += 1
+            off[mu] += 1
+        else:
+            pos[:, mu] -= 1
+            off[mu] -= 1
+            P = P @ dag(link(mu))
+    return P, tuple(off)
+
+
+def apply_at(U, c, psi, sites, bc=(1, 1, 1, 1)):
+    """(M psi) at the listed site indices only, [n, 4, 3]: every gauge path of the action is
+    evaluated site by site, so the cost does not grow with the lattice volume (apart from u0)."""
+    T, Z, Y, X = U.shape[:4]
+    sizes = np.array([X, Y, Z, T])
+    sites = np.asarray(sites, dtype=np.int64)
+    coords = np.stack([sites % X, (sites // X) % Y, (sites // (X * Y)) % Z, sites // (X * Y * Z)], axis=1)
+    grouped = collect(action_terms(c), resolve_u0(U, c))
+    out = np.zeros((len(sites), 12), dtype=np.complex128)
+    for w, s in grouped.items():
+        P, off = path_at(U, w, coords)
+        tgt = coords + np.array(off)
+        wraps = np.floor_divide(tgt, sizes)
+        sign = np.ones(len(sites))
+        for mu in range(4):
+            if bc[mu] == -1:
+                sign = sign * np.where(wraps[:, mu] % 2 == 0, 1.0, -1.0)
+        t = np.mod(tgt, sizes)
+        nb = psi[t[:, 3], t[:, 2], t[:, 1], t[:, 0]] * sign[:, None, None]
+        out += np.einsum("ab,ncd,nbd->nac", s, P, nb).reshape(len(sites), 12)
+    return out.reshape(len(sites), 4, 3)

@@ -51,7 +51,8 @@ def blk(A, B, C, D):
 
 
 def forward_parts(U, c):
-    """The forward matrices and their 6x6 blocks (Eqs. shifted_W_first .. shifted_W_last)."""
+    """The forward matrices (Eqs. shifted_W_first .. shifted_W_last), each kept as its quad of 6x6
+    blocks (A, B, C, D) = [[A, B], [C, D]] (None = 0)."""
     u0 = resolve_u0(U, c)
     E, B = clover_EB(U)
     Ul = [link(U, mu) for mu in range(4)]
@@ -62,8 +63,8 @@ def forward_parts(U, c):
     # W^0 = u0/(2 kappa) + [[D0, S0], [-S0, D0]]
     D0 = -(c.c_B * c.zeta + 16.0 * c.c5) / (2.0 * u0 ** 3) * BD
     S0 = -(c.c_E * c.zeta) / (2.0 * u0 ** 3) * ES
-    W0 = blk(D0, S0, -S0, D0) + u0 * p["inv2kappa"] * np.eye(12)
-    p["W0"] = W0
+    D0c = D0 + u0 * p["inv2kappa"] * np.eye(6)
+    p["W0"] = (D0c, S0, -S0, D0c)
 
     # W^+_4 = [[0, S4], [S4, -U4]], S4 = c_EE/(2 u0^4) (U4 ES(x+4) - ES(x) U4)
     U4 = one2(Ul[3])
@@ -71,7 +72,7 @@ def forward_parts(U, c):
     p["S+4"] = S4
     p["U4"] = U4
     Wp = [None] * 4
-    Wp[3] = blk(None, S4, S4, -U4)
+    Wp[3] = (None, S4, S4, -U4)
 
     # W^+_i = [[D+, S+], [S+, D+]]
     Dp, Sp = [None] * 3, [None] * 3
@@ -96,7 +97,7 @@ def forward_parts(U, c):
         D = D + c.c5 / u0 ** 4 * (Ui @ shift(BD, i) + BD @ Ui
                                   - 1j * sc(PAULI[i], Ul[i] @ shift(B[i], i) + B[i] @ Ul[i]))
         Dp[i], Sp[i] = D, S
-        Wp[i] = blk(D, S, S, D)
+        Wp[i] = (D, S, S, D)
     p["D+"], p["S+"], p["W+"] = Dp, Sp, Wp
 
     # W^{++}_ii = [[D++, S++], [S++, D++]]
@@ -105,7 +106,7 @@ def forward_parts(U, c):
         UU = Ul[i] @ shift(Ul[i], i)
         Dpp[i] = c.c4 / u0 * one2(UU)
         Spp[i] = (c.c1 + 2.0 * c.c2) / (2.0 * u0) * sc(PAULI[i], UU)
-        Wpp[i] = blk(Dpp[i], Spp[i], Spp[i], Dpp[i])
+        Wpp[i] = (Dpp[i], Spp[i], Spp[i], Dpp[i])
     p["D++"], p["S++"], p["W++ii"] = Dpp, Spp, Wpp
 
     # W^{++}_ij, W^{+-}_ij (i != j) = [[0, S], [S, 0]]
@@ -120,8 +121,8 @@ def forward_parts(U, c):
             Spm_ij = c.c2 / (2.0 * u0) * sc(PAULI[i] - PAULI[j],
                                             Ui @ dag(shift_vec(Uj, _vec({j: -1, i: 1})))
                                             + dag(shift(Uj, j, -1)) @ shift(Ui, j, -1))
-            Wppij[(i, j)] = blk(None, Spp_ij, Spp_ij, None)
-            Wpmij[(i, j)] = blk(None, Spm_ij, Spm_ij, None)
+            Wppij[(i, j)] = (None, Spp_ij, Spp_ij, None)
+            Wpmij[(i, j)] = (None, Spm_ij, Spm_ij, None)
     p["W++ij"], p["W+-ij"] = Wppij, Wpmij
     return p
 
@@ -133,42 +134,53 @@ def _vec(d):
     return v
 
 
+def qdag(q):
+    """Hermitian conjugate (spin and colour) of a quad: [[A, B], [C, D]]^dag = [[A^d, C^d], [B^d, D^d]]."""
+    A, B, C, D = q
+    d = lambda m: None if m is None else dag(m)
+    return (d(A), d(C), d(B), d(D))
+
+
+def qmap(q, f):
+    return tuple(None if m is None else f(m) for m in q)
+
+
 def backward_parts(p):
-    """W^-_mu, W^{--}_ii (Eq. opp_diag_pre_mat) and W^{--}_ij, W^{+-}_ji (Eq. conjugate)."""
+    """W^-_mu, W^{--}_ii (Eq. opp_diag_pre_mat) and W^{--}_ij, W^{+-}_ji (Eq. conjugate), as quads."""
     q = {}
     Wm = [None] * 4
     U4m = shift(p["U4"], 3, -1)
     S4m = shift(p["S+4"], 3, -1)
-    Wm[3] = blk(-dag(U4m), -dag(S4m), -dag(S4m), None)
+    Wm[3] = (-dag(U4m), -dag(S4m), -dag(S4m), None)
     for i in range(3):
         Dm = dag(shift(p["D+"][i], i, -1))
         Sm = dag(shift(p["S+"][i], i, -1))
-        Wm[i] = blk(Dm, -Sm, -Sm, Dm)
+        Wm[i] = (Dm, -Sm, -Sm, Dm)
     q["W-"] = Wm
     Wmm = [None] * 3
     for i in range(3):
         Dm = dag(shift(p["D++"][i], i, -2))
         Sm = dag(shift(p["S++"][i], i, -2))
-        Wmm[i] = blk(Dm, -Sm, -Sm, Dm)
+        Wmm[i] = (Dm, -Sm, -Sm, Dm)
     q["W--ii"] = Wmm
     Wmmij, Wmpji = {}, {}
     for i in range(3):
         for j in range(i + 1, 3):
             # W^{--}_{ij,x} = -W^{++ dagger}_{ij, x-i-j}
-            Wmmij[(i, j)] = -dag(shift_vec(p["W++ij"][(i, j)], _vec({i: -1, j: -1})))
+            Wmmij[(i, j)] = qmap(qdag(p["W++ij"][(i, j)]), lambda m: -shift_vec(m, _vec({i: -1, j: -1})))
             # W^{+-}_{ji,x} = -W^{+- dagger}_{ij, x-i+j}
-            Wmpji[(j, i)] = -dag(shift_vec(p["W+-ij"][(i, j)], _vec({i: -1, j: 1})))
+            Wmpji[(j, i)] = qmap(qdag(p["W+-ij"][(i, j)]), lambda m: -shift_vec(m, _vec({i: -1, j: 1})))
     q["W--ij"], q["W+-ji"] = Wmmij, Wmpji
     return q
 
 
-def blocks(U, c):
-    """{offset: 12x12 field} of Eq. minFlopForm (27 offsets)."""
+def quads(U, c):
+    """{offset: quad} for the 27 offsets of Eq. minFlopForm."""
     p = forward_parts(U, c)
     q = backward_parts(p)
     out = {(0, 0, 0, 0): p["W0"]}
     for mu in range(4):
-        out[tuple(_vec({mu: 1}))] = p["W+"][mu] if mu < 3 else blk(None, p["S+4"], p["S+4"], -p["U4"])
+        out[tuple(_vec({mu: 1}))] = p["W+"][mu]
         out[tuple(_vec({mu: -1}))] = q["W-"][mu]
     for i in range(3):
         out[tuple(_vec({i: 2}))] = p["W++ii"][i]
@@ -182,23 +194,57 @@ def blocks(U, c):
     return out
 
 
+def blocks(U, c):
+    """{offset: 12x12 field} of Eq. minFlopForm (27 offsets)."""
+    return {off: blk(*q) for off, q in quads(U, c).items()}
+
+
 def forward_set(U, c):
     """The 14 forward matrices per site, keyed by name, each a 12x12 field:
     'W0', 'W+x', 'W+y', 'W+z', 'W+t', 'W++xx', 'W++yy', 'W++zz', 'W++xy', 'W++xz', 'W++yz',
     'W+-xy', 'W+-xz', 'W+-yz' (the last three multiply psi_{x+i-j})."""
     p = forward_parts(U, c)
     n = "xyzt"
-    out = {"W0": p["W0"]}
+    out = {"W0": blk(*p["W0"])}
     for mu in range(4):
-        out["W+" + n[mu]] = p["W+"][mu] if mu < 3 else blk(None, p["S+4"], p["S+4"], -p["U4"])
+        out["W+" + n[mu]] = blk(*p["W+"][mu])
     for i in range(3):
-        out["W++" + n[i] * 2] = p["W++ii"][i]
-    for i in range(3):
-        for j in range(i + 1, 3):
-            out["W++" + n[i] + n[j]] = p["W++ij"][(i, j)]
+        out["W++" + n[i] * 2] = blk(*p["W++ii"][i])
     for i in range(3):
         for j in range(i + 1, 3):
-            out["W+-" + n[i] + n[j]] = p["W+-ij"][(i, j)]
+            out["W++" + n[i] + n[j]] = blk(*p["W++ij"][(i, j)])
+    for i in range(3):
+        for j in range(i + 1, 3):
+            out["W+-" + n[i] + n[j]] = blk(*p["W+-ij"][(i, j)])
+    return out
+
+
+def _qmv(q, v):
+    """[[A, B], [C, D]] applied to the spinor field v [..., 4, 3] without forming 12x12 matrices."""
+    shp = v.shape[:4]
+    up = v[..., 0:2, :].reshape(shp + (6,))
+    lo = v[..., 2:4, :].reshape(shp + (6,))
+    A, B, C, D = q
+    mv = lambda M, x: np.einsum("...ij,...j->...i", M, x)
+    ou = np.zeros(shp + (6,), dtype=np.complex128)
+    ol = np.zeros(shp + (6,), dtype=np.complex128)
+    if A is not None:
+        ou += mv(A, up)
+    if B is not None:
+        ou += mv(B, lo)
+    if C is not None:
+        ol += mv(C, up)
+    if D is not None:
+        ol += mv(D, lo)
+    return np.concatenate([ou.reshape(shp + (2, 3)), ol.reshape(shp + (2, 3))], axis=-2)
+
+
+def apply_lean(U, c, psi, bc=(1, 1, 1, 1)):
+    """M psi by Eq. minFlopForm, multiplying the 6x6 blocks directly (no 12x12 matrices), for
+    lattices where the dense blocks would not fit in memory."""
+    out = np.zeros_like(psi, dtype=np.complex128)
+    for off, q in quads(U, c).items():
+        out += _qmv(q, neighbour_spinor(psi, off, bc))
     return out
 
 
@@ -234,9 +280,9 @@ def apply_final_form(U, c, psi, bc=(1, 1, 1, 1)):
     def nb(mu, sgn):
         return neighbour_spinor(psi, _vec({mu: sgn}), bc)
 
-    out = _mv(p["W0"], psi)
+    out = _mv(blk(*p["W0"]), psi)
     for mu in range(4):
-        Wp = p["W+"][mu] if mu < 3 else blk(None, p["S+4"], p["S+4"], -p["U4"])
+        Wp = blk(*p["W+"][mu])
         out += _mv(Wp, nb(mu, +1))
         if mu < 3:
             Dd, Sd = dag(p["D+"][mu]), dag(p["S+"][mu])
@@ -245,7 +291,7 @@ def apply_final_form(U, c, psi, bc=(1, 1, 1, 1)):
             Wm_shift = blk(-dag(p["U4"]), -dag(p["S+4"]), -dag(p["S+4"]), None)
         out += t(_mv(Wm_shift, psi), mu, -1)
     for i in range(3):
-        A = shift(p["W++ii"][i], i, -1)                            # W^{++}_{ii, x-i}
+        A = shift(blk(*p["W++ii"][i]), i, -1)                      # W^{++}_{ii, x-i}
         out += t(_mv(A, nb(i, +1)), i, +1)
         Dd = dag(shift(p["D++"][i], i, -1))
         Sd = dag(shift(p["S++"][i], i, -1))
@@ -253,8 +299,8 @@ def apply_final_form(U, c, psi, bc=(1, 1, 1, 1)):
         out += t(_mv(Wmm_shift, nb(i, -1)), i, -1)
     for i in range(3):
         for j in range(i + 1, 3):
-            Bij = shift(p["W++ij"][(i, j)], j, -1)                 # W^{++}_{ij, x-j}
-            Cij = shift(p["W+-ij"][(i, j)], j, +1)                 # W^{+-}_{ij, x+j}
+            Bij = shift(blk(*p["W++ij"][(i, j)]), j, -1)           # W^{++}_{ij, x-j}
+            Cij = shift(blk(*p["W+-ij"][(i, j)]), j, +1)           # W^{+-}_{ij, x+j}
             out += t(_mv(Bij, nb(i, +1)), j, +1)
             out -= t(_mv(dag(Bij), nb(j, -1)), i, -1)
             out += t(_mv(Cij, nb(i, +1)), j, -1)

@@ -122,11 +122,11 @@ def test_conjugate_relations_hold_for_formula_built_matrices(rough_links):
             v = [0, 0, 0, 0]
             v[i] -= 1
             v[j] += 1
-            lhs = p["W+-ij"][(j, i)]
-            rhs = -dag(shift_vec(p["W+-ij"][(i, j)], v))
+            lhs = wform.blk(*p["W+-ij"][(j, i)])
+            rhs = -dag(shift_vec(wform.blk(*p["W+-ij"][(i, j)]), v))
             assert _max_rel(lhs, rhs) < 1e-13
             # W^{++}_{ij} is symmetric in i, j
-            assert _max_rel(p["W++ij"][(i, j)], p["W++ij"][(j, i)]) < 1e-13
+            assert _max_rel(wform.blk(*p["W++ij"][(i, j)]), wform.blk(*p["W++ij"][(j, i)])) < 1e-13
 
 
 def test_distinct_colour_blocks_of_the_stored_set(rough_links):
@@ -156,3 +156,18 @@ def test_distinct_colour_blocks_of_the_stored_set(rough_links):
         assert len(reps) == expected.get(name, 1), name
         total += len(reps)
     assert total == 40
+
+
+@pytest.mark.parametrize("dims,bc", [((4, 4, 4, 8), (1, 1, 1, 1)), ((3, 5, 4, 3), (1, -1, 1, -1))])
+def test_lean_and_per_site_evaluations_agree(dims, bc):
+    """The memory-lean W-form apply (6x6 blocks) and the per-site evaluation of the action give the
+    same M psi as the dense-block applies; these two are what full-size parity tests use."""
+    U = synth.random_links(dims, 0.4, 301)
+    c = synth.random_coeffs(302)
+    psi = synth.gaussian_source(dims, 303)
+    ref = wform.apply(U, c, psi, bc)
+    assert np.linalg.norm(wform.apply_lean(U, c, psi, bc) - ref) / np.linalg.norm(ref) < 1e-13
+    sites = np.array([0, 1, 7, 31, 32, 100, int(np.prod(dims)) - 1])
+    at = direct.apply_at(U, c, psi, sites, bc)
+    flat = ref.reshape(-1, 4, 3)[sites]
+    assert np.abs(at - flat).max() < 1e-13 * np.abs(flat).max()

@@ -44,7 +44,7 @@ def test_wrong_conjugate_relation_sign_is_caught(setup, monkeypatch):
 
     def bad(p):
         q = orig(p)
-        q["W--ij"] = {k: -v for k, v in q["W--ij"].items()}
+        q["W--ij"] = {k: wform.qmap(v, lambda m: -m) for k, v in q["W--ij"].items()}
         return q
     monkeypatch.setattr(wform, "backward_parts", bad)
     assert _mismatch(b1, wform.blocks(U, c)) > 1e-6
@@ -77,7 +77,9 @@ def test_missing_tadpole_power_is_caught(setup, monkeypatch):
     def bad(Ul, cc):
         p = orig(Ul, cc)
         u0 = p["u0"]
-        p["W0"] = (p["W0"] - u0 * p["inv2kappa"] * np.eye(12)) / u0 + u0 * p["inv2kappa"] * np.eye(12)
+        c0 = u0 * p["inv2kappa"] * np.eye(6)
+        A, B, C, D = p["W0"]
+        p["W0"] = ((A - c0) / u0 + c0, B / u0, C / u0, (D - c0) / u0 + c0)
         return p
     monkeypatch.setattr(wform, "forward_parts", bad)
     assert _mismatch(b1, wform.blocks(U, c)) > 1e-6
