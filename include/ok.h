@@ -1,0 +1,164 @@
+/*
+ * ok.h -- C ABI of the GB300 (sm_103a) library for the Oktay-Kronfeld (OK) action Dirac operator
+ * in the precalculated-W form of Jang et al., "Optimization of the Oktay-Kronfeld Action Conjugate
+ * Gradient Inverter" (PoS LATTICE2013, arXiv:1311.5029), and its BiCGStab inverter.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: dims = {X, Y, Z, T}; sites are ordered lexicographically with x fastest,
+ *   site = x + X * (y + Y * (z + Z * t)).  Direction mu = 0, 1, 2, 3 is x, y, z, t (the paper's
+ *   mu = 4 is t).  bc[mu] = +1 periodic, -1 antiperiodic boundary for the fermion field; the
+ *   gauge field is always periodic.
+ * Gauge links: [T][Z][Y][X][mu=4][3][3] complex (row-major 3x3), interleaved re/im, complex128
+ *   (OK_F64) or complex64 (OK_F32).
+ * Fermion fields: [T][Z][Y][X][spin=4][colour=3] complex, spin outer.  Spin basis: the Dirac
+ *   representation of the paper's Ref. [EKM] as fixed by the block forms of W (Sec. 2.2):
+ *   gamma_4 = diag(1, 1, -1, -1), gamma_i = [[0, sigma_i], [sigma_i, 0]].
+ * Pointers: every array argument is a DEVICE pointer owned by the caller (for example
+ *   torch.Tensor.data_ptr()), unless stated otherwise.  The library never frees caller memory.
+ *   `stream` is a cudaStream_t (NULL = the legacy default stream); all work is enqueued on it.
+ * Errors: every int-returning call returns OK_SUCCESS (0) or a negative OK_E* code and never
+ *   throws across the ABI.  OK_ECUDA means a CUDA runtime call failed; the CUDA error is
+ *   available from ok_last_cuda_error().  On any error no output is guaranteed.
+ * Threads: a W handle is immutable after ok_precompute_W; concurrent applies and solves with
+ *   the same handle on different streams are safe (each solve allocates its own workspace).
+ */
+#ifndef OK_GB300_H
+#define OK_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define OK_SUCCESS      0
+#define OK_EINVAL      -1   /* invalid argument (null pointer, bad size, missing precision) */
+#define OK_ENOMEM      -2   /* device or host allocation failed */
+#define OK_ECUDA       -3   /* a CUDA runtime call or kernel launch failed */
+#define OK_ENOCONV     -4   /* solver hit maxiter (or max restarts) before reaching tol */
+#define OK_EBREAKDOWN  -5   /* BiCGStab breakdown that restarts could not cure */
+#define OK_ENONFINITE  -6   /* a non-finite value appeared in a solver scalar */
+#define OK_EINTERNAL   -7   /* internal consistency check failed */
+
+/* ------------------------------------------------------------------ types */
+typedef struct {
+    int dims[4];   /* X, Y, Z, T; each >= 1, product <= OK_MAX_SITES */
+    int bc[4];     /* +1 periodic, -1 antiperiodic (fermion boundary phase) */
+} ok_lattice;
+
+#define OK_MAX_SITES (1 << 27)
+
+typedef enum { OK_F64 = 0, OK_F32 = 1 } ok_prec;
+
+/* Which stored precisions a W handle carries (bit mask for ok_precompute_W). */
+#define OK_W_F64 1
+#define OK_W_F32 2
+
+/* Coefficients of the tree-level, tadpole-improved OK action (Sec. 1; they enter the W formulas,
+ * Eqs. shifted_W_first .. shifted_W_last).  u0 <= 0: u0 is computed from the mean plaquette of
+ * the links.  kappa <= 0: 1/(2 kappa) = am0 + 1 + 3 r_s zeta + 18 c4. */
+typedef struct {
+    double u0, am0, kappa;
+    double zeta, r_s, c_B, c_E, c_EE, c1, c2, c3, c4, c5;
+} ok_coeffs;
+
+typedef struct {
+    int iters;             /* BiCGStab iterations (each = two applications of M) */
+    int restarts;          /* restarts from the true residual (breakdown or stagnation) */
+    int reliable_updates;  /* FP64 residual recomputations of the mixed-precision solver */
+    int fp64_applies;      /* FP64 applications of M, including true-residual checks */
+    double true_relres;    /* |b - M x| / |b| recomputed in FP64 at exit */
+    double iter_relres;    /* iterated residual norm / |b| at exit */
+    double time_ms;        /* host wall time of the call */
+} ok_solve_info;
+
+#define OK_SOLVE_AUTO   0  /* mixed if the handle has OK_W_F32 and OK_W_F64, else plain FP64 */
+#define OK_SOLVE_F64    1  /* plain FP64 BiCGStab (needs OK_W_F64) */
+#define OK_SOLVE_MIXED  2  /* FP32 BiCGStab with FP64 reliable updates (needs both precisions) */
+
+typedef struct {
+    double tol;          /* stop when |b - M x| / |b| < tol (true FP64 residual) */
+    int maxiter;         /* total BiCGStab iterations allowed */
+    int mode;            /* OK_SOLVE_* */
+    double delta;        /* mixed mode: reliable update when |r| < delta * max |r| since last */
+    int max_restarts;    /* restarts from the true residual allowed */
+    int check_every;     /* iterations enqueued between host convergence checks (>= 1) */
+} ok_solve_params;
+
+typedef struct ok_W ok_W;  /* opaque, library-owned precalculation-matrix set */
+
+/* ------------------------------------------------------------------ entry points */
+
+/* Precompute the W matrices (Sec. 2.2, "Precalculation"; Eqs. shifted_W_first ..
+ * shifted_W_last) for one gauge configuration: mean plaquette and u0, clover fields E_i and B_i,
+ * and the forward set W^0_x, W^+_{mu,x}, W^{++}_{ii,x}, W^{++}_{ij,x}, W^{+-}_{ij,x} (i < j) per
+ * site, unshifted, in a private site-blocked layout.  The backward matrices are not stored: they
+ * follow from the forward ones by Eqs. conjugate and opp_diag_pre_mat.  Arithmetic is FP64;
+ * W_precs selects the stored copies (OK_W_F64 and/or OK_W_F32).
+ *   links: device [T][Z][Y][X][4][3][3] complex in links_prec; not retained after the call.
+ *   W_out: receives a new handle owned by the caller, released with ok_free_W.
+ * Synchronises `stream` before returning (u0 is read back).  Errors: OK_EINVAL (null pointer,
+ * dims out of range, bad bc or mask), OK_ENOMEM, OK_ECUDA. */
+int ok_precompute_W(const ok_lattice* lat, const void* links, ok_prec links_prec,
+                    const ok_coeffs* coeffs, int W_precs, void* stream, ok_W** W_out);
+
+/* Release a handle from ok_precompute_W (NULL is ignored).  Frees device memory; call it only
+ * after work using the handle has completed. */
+void ok_free_W(ok_W* W);
+
+/* u0 used by the handle (given or computed from the mean plaquette); NaN if W is NULL. */
+double ok_W_u0(const ok_W* W);
+
+/* Mean plaquette (1/3) Re tr U_plaq over all sites and six planes; its fourth root is u0. */
+double ok_W_plaquette(const ok_W* W);
+
+/* Lattice, stored-precision mask and device bytes held by the handle.  Any output may be NULL. */
+int ok_W_info(const ok_W* W, ok_lattice* lat, int* W_precs, size_t* bytes);
+
+/* out = M psi (Eq. dslash with M in the form of Eq. minFlopForm: the on-site W^0, the 8 nearest,
+ * 6 next-to-nearest straight and 12 diagonal neighbours), using the handle's stored matrices of
+ * precision `prec`, arithmetic in that precision.
+ *   psi, out: device [V][4][3] complex in `prec`; out must not overlap psi.
+ * Errors: OK_EINVAL (null, aliasing, handle lacks `prec`), OK_ECUDA.  Asynchronous. */
+int ok_apply_M(const ok_W* W, ok_prec prec, const void* psi, void* out, void* stream);
+
+/* Solve M x = src by BiCGStab (the paper's bi-stabilized CG, Sec. 2.3) with default parameters
+ * (OK_SOLVE_AUTO, delta 0.1, 5 restarts).  src, x: device [V][4][3] complex128; x holds the
+ * initial guess on entry and the solution on exit.  info (host, may be NULL) is filled on
+ * success and on OK_ENOCONV / OK_EBREAKDOWN.  Synchronises `stream`. */
+int ok_bicgstab(const ok_W* W, const void* src, void* x, double tol, int maxiter,
+                ok_solve_info* info, void* stream);
+
+/* As ok_bicgstab with explicit parameters (params on the host). */
+int ok_bicgstab_ex(const ok_W* W, const void* src, void* x, const ok_solve_params* params,
+                   ok_solve_info* info, void* stream);
+
+/* The defaults used by ok_bicgstab, for the given tol and maxiter. */
+ok_solve_params ok_default_solve_params(double tol, int maxiter);
+
+/* True residual |b - M x| / |b| in FP64 (the check that judges every solve): one FP64
+ * application of M fused with the norms.  b, x: device [V][4][3] complex128; relres: host.
+ * Needs OK_W_F64.  Synchronises `stream`.  |b| = 0 gives relres = |M x|. */
+int ok_true_residual(const ok_W* W, const void* b, const void* x, double* relres, void* stream);
+
+/* Inspection: write the dense 12x12 forward matrix of one kind for every site, reconstructed from
+ * the stored representation of precision `prec`: out = device [V][12][12] complex128 (row index
+ * 3*spin + colour).  kind: 0 W^0; 1..4 W^+_mu (x, y, z, t); 5..7 W^{++}_ii (x, y, z);
+ * 8..10 W^{++}_ij (xy, xz, yz); 11..13 W^{+-}_ij (xy, xz, yz; they multiply psi_{x+i-j}). */
+int ok_W_expand(const ok_W* W, ok_prec prec, int kind, void* out, void* stream);
+
+/* Number of kernels this library has launched since it was loaded (all devices, all threads). */
+unsigned long long ok_launch_count(void);
+
+/* Last CUDA error code seen by the library on this thread (0 if none). */
+int ok_last_cuda_error(void);
+
+/* Static description of a status code. */
+const char* ok_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OK_GB300_H */

@@ -1,0 +1,271 @@
+"""Python binding of libokgb300.so, the GB300 (sm_103a) library for the Oktay-Kronfeld action
+Dirac operator in the precalculated-W form (Jang et al., PoS LATTICE2013, arXiv:1311.5029) and its
+BiCGStab inverter.
+
+The binding only marshals arguments: tensors are passed to the C ABI of include/ok.h as raw
+device pointers together with the current CUDA stream, and every step of the computation runs in
+the library's kernels.  PyTorch supplies device memory and streams.  If the library cannot be
+loaded the calls raise; there is no CPU fallback.
+
+Field layouts (device tensors, contiguous):
+  links  [T, Z, Y, X, 4, 3, 3] complex128 or complex64   (mu = x, y, z, t)
+  psi    [T, Z, Y, X, 4, 3]    complex128 (FP64) or complex64 (FP32), spin outer
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from .build import LIB, build as build_library
+
+__all__ = [
+    "load", "precompute_W", "apply_M", "bicgstab", "true_residual", "W_expand", "launch_count",
+    "strerror", "OKError", "WHandle", "F64", "F32", "W_F64", "W_F32", "SOLVE_AUTO", "SOLVE_F64",
+    "SOLVE_MIXED", "header_functions",
+]
+
+F64, F32 = 0, 1
+W_F64, W_F32 = 1, 2
+SOLVE_AUTO, SOLVE_F64, SOLVE_MIXED = 0, 1, 2
+OK_ENOCONV, OK_EBREAKDOWN = -4, -5
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ok.h")
+
+_COEFF_NAMES = ["u0", "am0", "kappa", "zeta", "r_s", "c_B", "c_E", "c_EE", "c1", "c2", "c3", "c4", "c5"]
+
+
+class ok_lattice(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("bc", ctypes.c_int * 4)]
+
+
+class ok_coeffs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in _COEFF_NAMES]
+
+
+class ok_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("fp64_applies", ctypes.c_int), ("true_relres", ctypes.c_double),
+                ("iter_relres", ctypes.c_double), ("time_ms", ctypes.c_double)]
+
+
+class ok_solve_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("mode", ctypes.c_int),
+                ("delta", ctypes.c_double), ("max_restarts", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class OKError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} ({status})")
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libokgb300.so (building it first if it is missing); raises if that fails."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        build_library()
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "ok_precompute_W": (i, [ctypes.POINTER(ok_lattice), vp, i, ctypes.POINTER(ok_coeffs), i, vp,
+                                ctypes.POINTER(vp)]),
+        "ok_free_W": (None, [vp]),
+        "ok_W_u0": (d, [vp]),
+        "ok_W_plaquette": (d, [vp]),
+        "ok_W_info": (i, [vp, ctypes.POINTER(ok_lattice), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_size_t)]),
+        "ok_apply_M": (i, [vp, i, vp, vp, vp]),
+        "ok_bicgstab": (i, [vp, vp, vp, d, i, ctypes.POINTER(ok_solve_info), vp]),
+        "ok_bicgstab_ex": (i, [vp, vp, vp, ctypes.POINTER(ok_solve_params), ctypes.POINTER(ok_solve_info), vp]),
+        "ok_default_solve_params": (ok_solve_params, [d, i]),
+        "ok_true_residual": (i, [vp, vp, vp, ctypes.POINTER(d), vp]),
+        "ok_W_expand": (i, [vp, i, i, vp, vp]),
+        "ok_launch_count": (ctypes.c_ulonglong, []),
+        "ok_last_cuda_error": (i, []),
+        "ok_strerror": (ctypes.c_char_p, [i]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_functions(path: str = HEADER) -> list:
+    """Names of the functions declared in include/ok.h."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ok_\w+)\s*\(", text)))
+
+
+def strerror(status: int) -> str:
+    return load().ok_strerror(int(status)).decode()
+
+
+def launch_count() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(load().ok_launch_count())
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise OKError(status, where)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need_cuda(t, dtypes, name):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name} has dtype {t.dtype}, expected one of {dtypes}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _coeffs(c) -> ok_coeffs:
+    get = (lambda k: c[k]) if isinstance(c, dict) else (lambda k: getattr(c, k))
+    return ok_coeffs(*[float(get(n)) for n in _COEFF_NAMES])
+
+
+class WHandle:
+    """Library-owned W matrices for one gauge configuration (freed with the object)."""
+
+    def __init__(self, ptr, dims, bc, precs):
+        self._ptr = ctypes.c_void_p(ptr)
+        self.dims = tuple(dims)
+        self.bc = tuple(bc)
+        self.precs = precs
+        self.volume = dims[0] * dims[1] * dims[2] * dims[3]
+
+    @property
+    def ptr(self):
+        return self._ptr
+
+    @property
+    def u0(self) -> float:
+        return float(load().ok_W_u0(self._ptr))
+
+    @property
+    def plaquette(self) -> float:
+        return float(load().ok_W_plaquette(self._ptr))
+
+    @property
+    def nbytes(self) -> int:
+        b = ctypes.c_size_t(0)
+        _check(load().ok_W_info(self._ptr, None, None, ctypes.byref(b)), "ok_W_info")
+        return int(b.value)
+
+    def free(self):
+        if self._ptr is not None and self._ptr.value:
+            load().ok_free_W(self._ptr)
+        self._ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def precompute_W(links, coeffs, bc=(1, 1, 1, 1), precisions=W_F64, stream=None) -> WHandle:
+    """ok_precompute_W: W matrices of the gauge field `links` [T, Z, Y, X, 4, 3, 3]."""
+    import torch
+    _need_cuda(links, (torch.complex128, torch.complex64), "links")
+    if links.dim() != 7 or tuple(links.shape[4:]) != (4, 3, 3):
+        raise ValueError("links must have shape [T, Z, Y, X, 4, 3, 3]")
+    T, Z, Y, X = links.shape[:4]
+    lat = ok_lattice((ctypes.c_int * 4)(X, Y, Z, T), (ctypes.c_int * 4)(*[int(b) for b in bc]))
+    out = ctypes.c_void_p()
+    lp = F64 if links.dtype == torch.complex128 else F32
+    st = load().ok_precompute_W(ctypes.byref(lat), ctypes.c_void_p(links.data_ptr()), lp,
+                                ctypes.byref(_coeffs(coeffs)), int(precisions), _stream(stream),
+                                ctypes.byref(out))
+    _check(st, "ok_precompute_W")
+    return WHandle(out.value, (X, Y, Z, T), bc, precisions)
+
+
+def _field_check(W: WHandle, t, name):
+    import torch
+    _need_cuda(t, (torch.complex128, torch.complex64), name)
+    if t.numel() != W.volume * 12:
+        raise ValueError(f"{name} must hold V * 12 = {W.volume * 12} complex numbers")
+
+
+def apply_M(W: WHandle, psi, out=None, stream=None):
+    """ok_apply_M: out = M psi in the precision of psi (complex128 -> FP64, complex64 -> FP32)."""
+    import torch
+    _field_check(W, psi, "psi")
+    if out is None:
+        out = torch.empty_like(psi)
+    _field_check(W, out, "out")
+    if out.dtype != psi.dtype:
+        raise ValueError("out and psi must have the same dtype")
+    prec = F64 if psi.dtype == torch.complex128 else F32
+    st = load().ok_apply_M(W.ptr, prec, ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                           _stream(stream))
+    _check(st, "ok_apply_M")
+    return out
+
+
+def bicgstab(W: WHandle, src, x=None, tol=1e-10, maxiter=20000, mode=SOLVE_AUTO, delta=0.1, max_restarts=5,
+             check_every=8, stream=None, raise_on_noconv=True):
+    """ok_bicgstab_ex: solve M x = src (complex128).  Returns (x, info dict)."""
+    import torch
+    _field_check(W, src, "src")
+    if src.dtype != torch.complex128:
+        raise ValueError("src must be complex128")
+    if x is None:
+        x = torch.zeros_like(src)
+    _field_check(W, x, "x")
+    if x.dtype != torch.complex128:
+        raise ValueError("x must be complex128")
+    prm = ok_solve_params(float(tol), int(maxiter), int(mode), float(delta), int(max_restarts), int(check_every))
+    info = ok_solve_info()
+    st = load().ok_bicgstab_ex(W.ptr, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                               ctypes.byref(prm), ctypes.byref(info), _stream(stream))
+    d = {k: getattr(info, k) for k, _ in ok_solve_info._fields_}
+    d["status"] = st
+    if st != 0 and (raise_on_noconv or st not in (OK_ENOCONV, OK_EBREAKDOWN)):
+        raise OKError(st, "ok_bicgstab_ex")
+    return x, d
+
+
+def true_residual(W: WHandle, b, x, stream=None) -> float:
+    """ok_true_residual: |b - M x| / |b| with the FP64 W."""
+    import torch
+    for t, n in ((b, "b"), (x, "x")):
+        _field_check(W, t, n)
+        if t.dtype != torch.complex128:
+            raise ValueError(f"{n} must be complex128")
+    r = ctypes.c_double(0.0)
+    st = load().ok_true_residual(W.ptr, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                 ctypes.byref(r), _stream(stream))
+    _check(st, "ok_true_residual")
+    return float(r.value)
+
+
+def W_expand(W: WHandle, kind: int, prec=F64, stream=None):
+    """ok_W_expand: dense 12x12 forward matrix of one kind per site, [V, 12, 12] complex128."""
+    import torch
+    out = torch.empty((W.volume, 12, 12), dtype=torch.complex128, device="cuda")
+    st = load().ok_W_expand(W.ptr, int(prec), int(kind), ctypes.c_void_p(out.data_ptr()), _stream(stream))
+    _check(st, "ok_W_expand")
+    return out
+
+
+W_KINDS = ["W0", "W+x", "W+y", "W+z", "W+t", "W++xx", "W++yy", "W++zz", "W++xy", "W++xz", "W++yz",
+           "W+-xy", "W+-xz", "W+-yz"]

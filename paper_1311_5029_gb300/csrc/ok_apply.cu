@@ -1,0 +1,473 @@
+// M psi in the W form (Eq. minFlopForm): one thread per site gathers the on-site spinor and the
+// 26 neighbour spinors (x +- mu, x +- 2i, x +- i +- j) and multiplies them by the stored forward
+// matrices at x, or by the backward ones obtained on the fly from the forward matrices stored at
+// the neighbour (Eqs. conjugate and opp_diag_pre_mat: W^-_{mu,x} = gamma5 W^{+ dagger}_{mu,x-mu}
+// gamma5 and so on).
+//
+// Spin handling.  With psi = (u, l) its upper and lower 2-spin halves, every hop except W^0 is
+// block diagonal in h+- = u +- l, so the kernel accumulates
+//   acc+ = (out_u + out_l) / 2,   acc- = (out_u - out_l) / 2
+// (the 1/2 is folded into the stored matrices) and writes out_u = acc+ + acc-,
+// out_l = acc+ - acc- at the end.  W^0 is block diagonal in u -+ i l instead.  In this basis the
+// 148 colour matrix-vector products per site are the only dense work.
+//
+// Precision R = double or float: loads, arithmetic and stores in R.  Fused epilogues feed the
+// BiCGStab reductions (ok_reduce.cuh) without a second pass over the output.
+#include "ok_launch.cuh"
+
+namespace okgb {
+
+constexpr int APPLY_THREADS = 128;
+
+template <typename R> struct Half { cx<R> v[2][3]; };
+
+// ---------------------------------------------------------------------------- loads
+template <typename R>
+__device__ __forceinline__ void load_spinor(const cx<R>* __restrict__ psi, int site, cx<R> (&v)[12]);
+
+template <>
+__device__ __forceinline__ void load_spinor<double>(const cx<double>* __restrict__ psi, int site, cx<double> (&v)[12]) {
+  const double2* p = reinterpret_cast<const double2*>(psi) + (size_t)site * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    double2 d = __ldg(p + k);
+    v[k] = mk(d.x, d.y);
+  }
+}
+
+template <>
+__device__ __forceinline__ void load_spinor<float>(const cx<float>* __restrict__ psi, int site, cx<float> (&v)[12]) {
+  const float4* p = reinterpret_cast<const float4*>(psi) + (size_t)site * 6;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    float4 d = __ldg(p + k);
+    v[2 * k] = mk(d.x, d.y);
+    v[2 * k + 1] = mk(d.z, d.w);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void store_spinor(cx<R>* __restrict__ out, int site, const cx<R> (&v)[12]);
+
+template <>
+__device__ __forceinline__ void store_spinor<double>(cx<double>* __restrict__ out, int site, const cx<double> (&v)[12]) {
+  double2* p = reinterpret_cast<double2*>(out) + (size_t)site * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) p[k] = make_double2(v[k].re, v[k].im);
+}
+
+template <>
+__device__ __forceinline__ void store_spinor<float>(cx<float>* __restrict__ out, int site, const cx<float> (&v)[12]) {
+  float4* p = reinterpret_cast<float4*>(out) + (size_t)site * 6;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p[k] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
+}
+
+// Matrix m of the site record of `site`.
+template <typename R>
+__device__ __forceinline__ M3<R> wmat(const cx<R>* __restrict__ W, int site, int m) {
+  const size_t base = ((size_t)(site >> 5) * NMAT + m) * (9 * LANES) + (site & 31);
+  M3<R> a;
+  if constexpr (sizeof(R) == 8) {
+    const double2* p = reinterpret_cast<const double2*>(W) + base;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      double2 d = __ldg(p + e * LANES);
+      a.e[e] = mk<R>(d.x, d.y);
+    }
+  } else {
+    const float2* p = reinterpret_cast<const float2*>(W) + base;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      float2 d = __ldg(p + e * LANES);
+      a.e[e] = mk<R>(d.x, d.y);
+    }
+  }
+  return a;
+}
+
+// ---------------------------------------------------------------------------- colour algebra
+// y += A v, y -= A v, y += A^dag v, y -= A^dag v
+template <typename R> __device__ __forceinline__ void mv_add(cx<R> (&y)[3], const M3<R>& A, const cx<R> (&v)[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[r] = fma_c(A.e[3 * r + c], v[c], y[r]);
+}
+template <typename R> __device__ __forceinline__ void mv_sub(cx<R> (&y)[3], const M3<R>& A, const cx<R> (&v)[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[r] = fma_c(-A.e[3 * r + c], v[c], y[r]);
+}
+template <typename R> __device__ __forceinline__ void mdv_add(cx<R> (&y)[3], const M3<R>& A, const cx<R> (&v)[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[r] = fma_cj(A.e[3 * c + r], v[c], y[r]);
+}
+template <typename R> __device__ __forceinline__ void mdv_sub(cx<R> (&y)[3], const M3<R>& A, const cx<R> (&v)[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[r] = fma_cj(-A.e[3 * c + r], v[c], y[r]);
+}
+template <typename R> __device__ __forceinline__ void mv(cx<R> (&y)[3], const M3<R>& A, const cx<R> (&v)[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    y[r] = A.e[3 * r] * v[0];
+    y[r] = fma_c(A.e[3 * r + 1], v[1], y[r]);
+    y[r] = fma_c(A.e[3 * r + 2], v[2], y[r]);
+  }
+}
+template <typename R> __device__ __forceinline__ void mdv(cx<R> (&y)[3], const M3<R>& A, const cx<R> (&v)[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    y[r] = cj(A.e[r]) * v[0];
+    y[r] = fma_cj(A.e[3 + r], v[1], y[r]);
+    y[r] = fma_cj(A.e[6 + r], v[2], y[r]);
+  }
+}
+
+// ---------------------------------------------------------------------------- geometry
+// Neighbour x + d with fermion boundary sign; |d_mu| <= 2.
+template <int D0, int D1, int D2, int D3>
+__device__ __forceinline__ int nbr_site(const int (&c)[4], const Geom& g, bool& neg) {
+  const int d[4] = {D0, D1, D2, D3};
+  int idx = 0, stride = 1;
+  neg = false;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    int x = c[mu];
+    if (d[mu] != 0) {
+      const int L = g.L[mu];
+      int y = x + d[mu];
+      int q = (y + 2 * L) / L - 2;  // floor(y / L) for y >= -2L
+      x = y - q * L;
+      if ((g.bcneg >> mu) & q & 1) neg = !neg;
+    }
+    idx += x * stride;
+    stride *= g.L[mu];
+  }
+  return idx;
+}
+
+// Gather the neighbour at offset d and form h+ = u + l, h- = u - l (with the boundary sign).
+template <typename R, int D0, int D1, int D2, int D3>
+__device__ __forceinline__ int gather_h(const cx<R>* __restrict__ psi, const int (&c)[4], const Geom& g,
+                                        Half<R>& hp, Half<R>& hm, Half<R>* up = nullptr, Half<R>* lo = nullptr) {
+  bool neg;
+  int n = nbr_site<D0, D1, D2, D3>(c, g, neg);
+  cx<R> v[12];
+  load_spinor<R>(psi, n, v);
+  if (neg) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = -v[k];
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      hp.v[s][a] = v[3 * s + a] + v[3 * (s + 2) + a];
+      hm.v[s][a] = v[3 * s + a] - v[3 * (s + 2) + a];
+      if (up) up->v[s][a] = v[3 * s + a];
+      if (lo) lo->v[s][a] = v[3 * (s + 2) + a];
+    }
+  return n;
+}
+
+// ---------------------------------------------------------------------------- hop kernels
+// acc0 += B00 h0 + B01 h1, acc1 += B10 h0 + B11 h1 (blocks at matrices m .. m+3 of `site`);
+// DAG: acc0 += B00^dag h0 + B10^dag h1, acc1 += B01^dag h0 + B11^dag h1.
+template <typename R, bool DAG>
+__device__ __forceinline__ void block2(const cx<R>* __restrict__ W, int site, int m, const Half<R>& h, Half<R>& acc) {
+  M3<R> b;
+  b = wmat(W, site, m + 0);
+  if (DAG) mdv_add(acc.v[0], b, h.v[0]); else mv_add(acc.v[0], b, h.v[0]);
+  b = wmat(W, site, m + 1);
+  if (DAG) mdv_add(acc.v[1], b, h.v[0]); else mv_add(acc.v[0], b, h.v[1]);
+  b = wmat(W, site, m + 2);
+  if (DAG) mdv_add(acc.v[0], b, h.v[1]); else mv_add(acc.v[1], b, h.v[0]);
+  b = wmat(W, site, m + 3);
+  if (DAG) mdv_add(acc.v[1], b, h.v[1]); else mv_add(acc.v[1], b, h.v[1]);
+}
+
+// sigma_k on a 2-spinor: out = sigma_k y  (k = 0, 1, 2 for x, y, z), added with factor f (+1 or -1)
+template <typename R>
+__device__ __forceinline__ void add_sigma(Half<R>& acc, int k, const Half<R>& y, R f) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (k == 0) {
+      acc.v[0][a] = acc.v[0][a] + f * y.v[1][a];
+      acc.v[1][a] = acc.v[1][a] + f * y.v[0][a];
+    } else if (k == 1) {
+      acc.v[0][a] = acc.v[0][a] + f * tmi(y.v[1][a]);
+      acc.v[1][a] = acc.v[1][a] + f * ti(y.v[0][a]);
+    } else {
+      acc.v[0][a] = acc.v[0][a] + f * y.v[0][a];
+      acc.v[1][a] = acc.v[1][a] - f * y.v[1][a];
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void add_scaled(Half<R>& acc, R f, const Half<R>& y) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      acc.v[s][a].re = fma(f, y.v[s][a].re, acc.v[s][a].re);
+      acc.v[s][a].im = fma(f, y.v[s][a].im, acc.v[s][a].im);
+    }
+}
+
+// y_s = V h_s or V^dag h_s for both spins
+template <typename R, bool DAG>
+__device__ __forceinline__ void colour2(Half<R>& y, const M3<R>& V, const Half<R>& h) {
+  if (DAG) { mdv(y.v[0], V, h.v[0]); mdv(y.v[1], V, h.v[1]); }
+  else { mv(y.v[0], V, h.v[0]); mv(y.v[1], V, h.v[1]); }
+}
+
+// Spatial nearest neighbours in direction I.
+template <typename R, int I>
+__device__ __forceinline__ void hop_spatial(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+                                            const Geom& g, int s, Half<R>& ap, Half<R>& am) {
+  constexpr int mp = M_WP + 8 * I, mm = mp + 4;
+  Half<R> hp, hm;
+  // forward: acc+ += (P+ / 2) h+, acc- += (P- / 2) h-, P at x
+  gather_h<R, I == 0, I == 1, I == 2, 0>(psi, c, g, hp, hm);
+  block2<R, false>(W, s, mp, hp, ap);
+  block2<R, false>(W, s, mm, hm, am);
+  // backward: acc+ += (P- / 2)^dag h+, acc- += (P+ / 2)^dag h-, P at x - I
+  int n = gather_h<R, -(I == 0), -(I == 1), -(I == 2), 0>(psi, c, g, hp, hm);
+  block2<R, true>(W, n, mm, hp, ap);
+  block2<R, true>(W, n, mp, hm, am);
+}
+
+// Temporal nearest neighbours: W^+_4 = [[0, S], [S, -U]], W^-_4 = [[-U^dag, -S^dag], [-S^dag, 0]].
+template <typename R>
+__device__ __forceinline__ void hop_time(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+                                         const Geom& g, int s, Half<R>& ap, Half<R>& am) {
+  Half<R> hp, hm, lo, up, w;
+  // forward at x: acc+ += S h+ - U l, acc- += U l - S h- (stored halves)
+  gather_h<R, 0, 0, 0, 1>(psi, c, g, hp, hm, nullptr, &lo);
+  {
+    M3<R> U = wmat(W, s, M_UT);
+    colour2<R, false>(w, U, lo);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { ap.v[q][a] = ap.v[q][a] - w.v[q][a]; am.v[q][a] = am.v[q][a] + w.v[q][a]; }
+    M3<R> s3 = wmat(W, s, M_ST + 0);
+    mv_add(ap.v[0], s3, hp.v[0]); mv_sub(ap.v[1], s3, hp.v[1]);
+    mv_sub(am.v[0], s3, hm.v[0]); mv_add(am.v[1], s3, hm.v[1]);
+    M3<R> n1 = wmat(W, s, M_ST + 1);
+    mv_add(ap.v[0], n1, hp.v[1]); mv_sub(am.v[0], n1, hm.v[1]);
+    M3<R> n2 = wmat(W, s, M_ST + 2);
+    mv_add(ap.v[1], n2, hp.v[0]); mv_sub(am.v[1], n2, hm.v[0]);
+  }
+  // backward from x - t: acc+ += -U^dag u - S^dag h+, acc- += -U^dag u + S^dag h-
+  int n = gather_h<R, 0, 0, 0, -1>(psi, c, g, hp, hm, &up, nullptr);
+  {
+    M3<R> U = wmat(W, n, M_UT);
+    colour2<R, true>(w, U, up);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { ap.v[q][a] = ap.v[q][a] - w.v[q][a]; am.v[q][a] = am.v[q][a] - w.v[q][a]; }
+    // S^dag = [[s3^dag, n2^dag], [n1^dag, -s3^dag]]
+    M3<R> s3 = wmat(W, n, M_ST + 0);
+    mdv_sub(ap.v[0], s3, hp.v[0]); mdv_add(ap.v[1], s3, hp.v[1]);
+    mdv_add(am.v[0], s3, hm.v[0]); mdv_sub(am.v[1], s3, hm.v[1]);
+    M3<R> n1 = wmat(W, n, M_ST + 1);
+    mdv_sub(ap.v[1], n1, hp.v[0]); mdv_add(am.v[1], n1, hm.v[0]);
+    M3<R> n2 = wmat(W, n, M_ST + 2);
+    mdv_sub(ap.v[0], n2, hp.v[1]); mdv_add(am.v[0], n2, hm.v[1]);
+  }
+}
+
+// Straight two-hop neighbours x +- 2I: W^{++}_ii = (a + b sigma_i) V on h+, (a - b sigma_i) V on h-.
+template <typename R, int I>
+__device__ __forceinline__ void hop_two(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+                                        const Geom& g, int s, R a, R b, Half<R>& ap, Half<R>& am) {
+  Half<R> hp, hm, y;
+  gather_h<R, 2 * (I == 0), 2 * (I == 1), 2 * (I == 2), 0>(psi, c, g, hp, hm);
+  M3<R> V = wmat(W, s, M_VII + I);
+  colour2<R, false>(y, V, hp);
+  add_scaled(ap, a, y); add_sigma(ap, I, y, b);
+  colour2<R, false>(y, V, hm);
+  add_scaled(am, a, y); add_sigma(am, I, y, -b);
+  int n = gather_h<R, -2 * (I == 0), -2 * (I == 1), -2 * (I == 2), 0>(psi, c, g, hp, hm);
+  V = wmat(W, n, M_VII + I);
+  colour2<R, true>(y, V, hp);
+  add_scaled(ap, a, y); add_sigma(ap, I, y, -b);
+  colour2<R, true>(y, V, hm);
+  add_scaled(am, a, y); add_sigma(am, I, y, b);
+}
+
+// Diagonal neighbours of the pair (I, J), I < J, P = pair index:
+//   x+I+J: acc+ += (s_I + s_J) V h+, acc- -= (s_I + s_J) V h-             (V at x)
+//   x-I-J: acc+ -= (s_I + s_J) V^dag h+, acc- += (s_I + s_J) V^dag h-     (V at x-I-J)
+//   x+I-J: acc+ += (s_I - s_J) X h+, acc- -= (s_I - s_J) X h-             (X at x)
+//   x-I+J: acc+ -= (s_I - s_J) X^dag h+, acc- += (s_I - s_J) X^dag h-     (X at x-I+J)
+template <typename R, int I, int J, int P>
+__device__ __forceinline__ void hop_diag(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+                                         const Geom& g, int s, Half<R>& ap, Half<R>& am) {
+  constexpr int A0 = (I == 0) + (J == 0), A1 = (I == 1) + (J == 1), A2 = (I == 2) + (J == 2);
+  constexpr int B0 = (I == 0) - (J == 0), B1 = (I == 1) - (J == 1), B2 = (I == 2) - (J == 2);
+  Half<R> hp, hm, y;
+  M3<R> V;
+  gather_h<R, A0, A1, A2, 0>(psi, c, g, hp, hm);
+  V = wmat(W, s, M_VIJ + P);
+  colour2<R, false>(y, V, hp); add_sigma(ap, I, y, R(1)); add_sigma(ap, J, y, R(1));
+  colour2<R, false>(y, V, hm); add_sigma(am, I, y, R(-1)); add_sigma(am, J, y, R(-1));
+  int n = gather_h<R, -A0, -A1, -A2, 0>(psi, c, g, hp, hm);
+  V = wmat(W, n, M_VIJ + P);
+  colour2<R, true>(y, V, hp); add_sigma(ap, I, y, R(-1)); add_sigma(ap, J, y, R(-1));
+  colour2<R, true>(y, V, hm); add_sigma(am, I, y, R(1)); add_sigma(am, J, y, R(1));
+  gather_h<R, B0, B1, B2, 0>(psi, c, g, hp, hm);
+  V = wmat(W, s, M_XIJ + P);
+  colour2<R, false>(y, V, hp); add_sigma(ap, I, y, R(1)); add_sigma(ap, J, y, R(-1));
+  colour2<R, false>(y, V, hm); add_sigma(am, I, y, R(-1)); add_sigma(am, J, y, R(1));
+  n = gather_h<R, -B0, -B1, -B2, 0>(psi, c, g, hp, hm);
+  V = wmat(W, n, M_XIJ + P);
+  colour2<R, true>(y, V, hp); add_sigma(ap, I, y, R(-1)); add_sigma(ap, J, y, R(1));
+  colour2<R, true>(y, V, hm); add_sigma(am, I, y, R(1)); add_sigma(am, J, y, R(-1));
+}
+
+// ---------------------------------------------------------------------------- the kernel
+template <typename R, int EPI>
+__global__ void __launch_bounds__(APPLY_THREADS) apply_kernel(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi,
+                                                              cx<R>* __restrict__ out, Geom g, R c0q, R a_ii, R b_ii,
+                                                              EpiArgs<R> ep) {
+  if (EPI != EPI_NONE && ep.halt && *ep.halt) return;
+  const int s = blockIdx.x * APPLY_THREADS + threadIdx.x;
+  double red[3] = {0.0, 0.0, 0.0};
+  if (s < g.V) {
+    int c[4];
+    {
+      int r = s;
+      c[0] = r % g.L[0]; r /= g.L[0];
+      c[1] = r % g.L[1]; r /= g.L[1];
+      c[2] = r % g.L[2]; c[3] = r / g.L[2];
+    }
+    Half<R> ap, am;
+    cx<R> x0[12];
+    // on-site: a = u - i l, b = u + i l; A = Y+ a, B = Y- b; acc+- = (A + B) +- i (A - B)
+    load_spinor<R>(psi, s, x0);
+    {
+      Half<R> a, b, A, B;
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          a.v[q][k] = x0[3 * q + k] - ti(x0[3 * (q + 2) + k]);
+          b.v[q][k] = x0[3 * q + k] + ti(x0[3 * (q + 2) + k]);
+          A.v[q][k] = c0q * a.v[q][k];
+          B.v[q][k] = c0q * b.v[q][k];
+        }
+      M3<R> y = wmat(W, s, M_Y0P + 0);
+      mv_add(A.v[0], y, a.v[0]); mv_sub(A.v[1], y, a.v[1]);
+      y = wmat(W, s, M_Y0P + 1);
+      mv_add(A.v[0], y, a.v[1]);
+      y = wmat(W, s, M_Y0P + 2);
+      mv_add(A.v[1], y, a.v[0]);
+      y = wmat(W, s, M_Y0M + 0);
+      mv_add(B.v[0], y, b.v[0]); mv_sub(B.v[1], y, b.v[1]);
+      y = wmat(W, s, M_Y0M + 1);
+      mv_add(B.v[0], y, b.v[1]);
+      y = wmat(W, s, M_Y0M + 2);
+      mv_add(B.v[1], y, b.v[0]);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          cx<R> P = A.v[q][k] + B.v[q][k], Q = A.v[q][k] - B.v[q][k];
+          ap.v[q][k] = P + ti(Q);
+          am.v[q][k] = P - ti(Q);
+        }
+    }
+    hop_spatial<R, 0>(W, psi, c, g, s, ap, am);
+    hop_spatial<R, 1>(W, psi, c, g, s, ap, am);
+    hop_spatial<R, 2>(W, psi, c, g, s, ap, am);
+    hop_time<R>(W, psi, c, g, s, ap, am);
+    hop_two<R, 0>(W, psi, c, g, s, a_ii, b_ii, ap, am);
+    hop_two<R, 1>(W, psi, c, g, s, a_ii, b_ii, ap, am);
+    hop_two<R, 2>(W, psi, c, g, s, a_ii, b_ii, ap, am);
+    hop_diag<R, 0, 1, 0>(W, psi, c, g, s, ap, am);
+    hop_diag<R, 0, 2, 1>(W, psi, c, g, s, ap, am);
+    hop_diag<R, 1, 2, 2>(W, psi, c, g, s, ap, am);
+
+    cx<R> o[12];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        o[3 * q + k] = ap.v[q][k] + am.v[q][k];
+        o[3 * (q + 2) + k] = ap.v[q][k] - am.v[q][k];
+      }
+    if (EPI == EPI_RESID) {
+      cx<R> bv[12];
+      load_spinor<R>(ep.b, s, bv);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        o[k] = bv[k] - o[k];
+        red[0] += (double)o[k].re * o[k].re + (double)o[k].im * o[k].im;
+        red[1] += (double)bv[k].re * bv[k].re + (double)bv[k].im * bv[k].im;
+      }
+    }
+    store_spinor<R>(out, s, o);
+    if (EPI == EPI_DOT) {
+      cx<R> rh[12];
+      load_spinor<R>(ep.rhat, s, rh);
+      cx<R> d = mk<R>(0, 0);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) d = fma_cj(rh[k], o[k], d);
+      red[0] = d.re;
+      red[1] = d.im;
+    } else if (EPI == EPI_TS) {
+      cx<R> d = mk<R>(0, 0);
+      R n2 = 0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        d = fma_cj(o[k], x0[k], d);
+        n2 += o[k].re * o[k].re + o[k].im * o[k].im;
+      }
+      red[0] = d.re;
+      red[1] = d.im;
+      red[2] = n2;
+    }
+  }
+  if (EPI == EPI_DOT || EPI == EPI_RESID) {
+    double v2[2] = {red[0], red[1]};
+    grid_reduce<2, APPLY_THREADS>(v2, ep.ra, ep.ticket);
+  } else if (EPI == EPI_TS) {
+    grid_reduce<3, APPLY_THREADS>(red, ep.ra, ep.ticket);
+  }
+}
+
+// ---------------------------------------------------------------------------- launchers
+template <typename R>
+int launch_apply(const ok_W* Wh, const cx<R>* psi, cx<R>* out, int epi, const EpiArgs<R>& ep, cudaStream_t st) {
+  const cx<R>* W = (const cx<R>*)(sizeof(R) == 8 ? Wh->W64 : Wh->W32);
+  if (!W) return OK_EINVAL;
+  const Geom& g = Wh->g;
+  int nb = grid_for(g.V, APPLY_THREADS);
+  R c0q = (R)Wh->sc.c0q, a = (R)Wh->sc.a_ii, b = (R)Wh->sc.b_ii;
+  switch (epi) {
+    case EPI_NONE: apply_kernel<R, EPI_NONE><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+    case EPI_DOT: apply_kernel<R, EPI_DOT><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+    case EPI_TS: apply_kernel<R, EPI_TS><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+    case EPI_RESID: apply_kernel<R, EPI_RESID><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+    default: return OK_EINVAL;
+  }
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+int apply_blocks_needed(const ok_W* Wh) { return grid_for(Wh->g.V, APPLY_THREADS); }
+
+template int launch_apply<double>(const ok_W*, const cx<double>*, cx<double>*, int, const EpiArgs<double>&, cudaStream_t);
+template int launch_apply<float>(const ok_W*, const cx<float>*, cx<float>*, int, const EpiArgs<float>&, cudaStream_t);
+
+}  // namespace okgb

@@ -1,0 +1,255 @@
+// BiCGStab vector updates with fused inner products (the "vector addition" work the paper times
+// in Table 1c).  Vectors are complex arrays of n = 12 V entries, processed in 16-byte units
+// (one complex double or two complex floats).  Every kernel first reads the solver's halt flag
+// so that iterations enqueued after convergence are no-ops; scalars (alpha, omega, beta) are read
+// from the device-resident state, so no host round trip is needed between kernels.
+#include "ok_launch.cuh"
+
+namespace okgb {
+
+constexpr int BLAS_THREADS = 256;
+
+template <typename R> struct Unit;
+template <> struct Unit<double> {
+  using T = double2;
+  static constexpr int NC = 1;
+  __device__ static __forceinline__ void get(const T& u, cx<double> (&c)[1]) { c[0] = mk(u.x, u.y); }
+  __device__ static __forceinline__ T put(const cx<double> (&c)[1]) { return make_double2(c[0].re, c[0].im); }
+};
+template <> struct Unit<float> {
+  using T = float4;
+  static constexpr int NC = 2;
+  __device__ static __forceinline__ void get(const T& u, cx<float> (&c)[2]) { c[0] = mk(u.x, u.y); c[1] = mk(u.z, u.w); }
+  __device__ static __forceinline__ T put(const cx<float> (&c)[2]) { return make_float4(c[0].re, c[0].im, c[1].re, c[1].im); }
+};
+
+template <typename R> __device__ __forceinline__ cx<R> scal(dcx z) { return mk<R>((R)z.re, (R)z.im); }
+
+#define OK_GRID_STRIDE(i, n) for (long long i = blockIdx.x * (long long)BLAS_THREADS + threadIdx.x; i < (n); i += (long long)gridDim.x * BLAS_THREADS)
+
+// s = r - alpha v
+template <typename R>
+__global__ void __launch_bounds__(BLAS_THREADS) update_s_kernel(const typename Unit<R>::T* __restrict__ r,
+                                                                const typename Unit<R>::T* __restrict__ v,
+                                                                typename Unit<R>::T* __restrict__ s, long long nu,
+                                                                const SolverState* __restrict__ st) {
+  if (st->halt) return;
+  using U = Unit<R>;
+  const cx<R> al = scal<R>(st->alpha);
+  OK_GRID_STRIDE(i, nu) {
+    cx<R> a[U::NC], b[U::NC];
+    U::get(r[i], a);
+    U::get(v[i], b);
+#pragma unroll
+    for (int k = 0; k < U::NC; ++k) a[k] = a[k] - al * b[k];
+    s[i] = U::put(a);
+  }
+}
+
+// x += alpha p + omega s;  r = s - omega t;  sums <rhat, r>, <r, r>  ->  FIN_XR
+template <typename R>
+__global__ void __launch_bounds__(BLAS_THREADS) update_xr_kernel(typename Unit<R>::T* __restrict__ x,
+                                                                 const typename Unit<R>::T* __restrict__ p,
+                                                                 const typename Unit<R>::T* __restrict__ s,
+                                                                 const typename Unit<R>::T* __restrict__ t,
+                                                                 typename Unit<R>::T* __restrict__ r,
+                                                                 const typename Unit<R>::T* __restrict__ rhat,
+                                                                 long long nu, SolverState* __restrict__ st,
+                                                                 RedArgs ra) {
+  if (st->halt) return;
+  using U = Unit<R>;
+  const cx<R> al = scal<R>(st->alpha), om = scal<R>(st->omega);
+  double red[3] = {0.0, 0.0, 0.0};
+  OK_GRID_STRIDE(i, nu) {
+    cx<R> xv[U::NC], pv[U::NC], sv[U::NC], tv[U::NC], hv[U::NC];
+    U::get(x[i], xv);
+    U::get(p[i], pv);
+    U::get(s[i], sv);
+    U::get(t[i], tv);
+    U::get(rhat[i], hv);
+    cx<R> d = mk<R>(0, 0);
+    R n2 = 0;
+#pragma unroll
+    for (int k = 0; k < U::NC; ++k) {
+      xv[k] = xv[k] + al * pv[k] + om * sv[k];
+      sv[k] = sv[k] - om * tv[k];
+      d = fma_cj(hv[k], sv[k], d);
+      n2 += sv[k].re * sv[k].re + sv[k].im * sv[k].im;
+    }
+    x[i] = U::put(xv);
+    r[i] = U::put(sv);
+    red[0] += d.re;
+    red[1] += d.im;
+    red[2] += n2;
+  }
+  grid_reduce<3, BLAS_THREADS>(red, ra, &st->ticket[2]);
+}
+
+// p = r + beta (p - omega v)
+template <typename R>
+__global__ void __launch_bounds__(BLAS_THREADS) update_p_kernel(typename Unit<R>::T* __restrict__ p,
+                                                                const typename Unit<R>::T* __restrict__ r,
+                                                                const typename Unit<R>::T* __restrict__ v,
+                                                                long long nu, const SolverState* __restrict__ st) {
+  if (st->halt) return;
+  using U = Unit<R>;
+  const cx<R> be = scal<R>(st->beta), om = scal<R>(st->omega);
+  OK_GRID_STRIDE(i, nu) {
+    cx<R> pv[U::NC], rv[U::NC], vv[U::NC];
+    U::get(p[i], pv);
+    U::get(r[i], rv);
+    U::get(v[i], vv);
+#pragma unroll
+    for (int k = 0; k < U::NC; ++k) pv[k] = rv[k] + be * (pv[k] - om * vv[k]);
+    p[i] = U::put(pv);
+  }
+}
+
+// Restart: rhat = p = r (same precision), sum <r, r> -> FIN_RESTART.
+template <typename R>
+__global__ void __launch_bounds__(BLAS_THREADS) restart_kernel(const typename Unit<R>::T* __restrict__ r,
+                                                               typename Unit<R>::T* __restrict__ rhat,
+                                                               typename Unit<R>::T* __restrict__ p, long long nu,
+                                                               SolverState* __restrict__ st, RedArgs ra) {
+  using U = Unit<R>;
+  double red[1] = {0.0};
+  OK_GRID_STRIDE(i, nu) {
+    typename U::T u = r[i];
+    rhat[i] = u;
+    p[i] = u;
+    cx<R> a[U::NC];
+    U::get(u, a);
+#pragma unroll
+    for (int k = 0; k < U::NC; ++k) red[0] += (double)a[k].re * a[k].re + (double)a[k].im * a[k].im;
+  }
+  grid_reduce<1, BLAS_THREADS>(red, ra, &st->ticket[3]);
+}
+
+// Mixed precision: r32 = (float) r64; RESTART: rhat = p = r32 and FIN_RESTART on <r, r>;
+// otherwise FIN_CONTINUE on <rhat, r32>, <r32, r32>.  Units are complex doubles here.
+template <bool RESTART>
+__global__ void __launch_bounds__(BLAS_THREADS) demote_kernel(const double2* __restrict__ r64, float2* __restrict__ r32,
+                                                              float2* __restrict__ rhat, float2* __restrict__ p,
+                                                              long long n, SolverState* __restrict__ st, RedArgs ra) {
+  double red[3] = {0.0, 0.0, 0.0};
+  OK_GRID_STRIDE(i, n) {
+    double2 d = r64[i];
+    float2 f = make_float2((float)d.x, (float)d.y);
+    r32[i] = f;
+    if (RESTART) {
+      rhat[i] = f;
+      p[i] = f;
+      red[0] += (double)f.x * f.x + (double)f.y * f.y;
+    } else {
+      float2 h = rhat[i];
+      red[0] += (double)h.x * f.x + (double)h.y * f.y;
+      red[1] += (double)h.x * f.y - (double)h.y * f.x;
+      red[2] += (double)f.x * f.x + (double)f.y * f.y;
+    }
+  }
+  if (RESTART) {
+    double v1[1] = {red[0]};
+    grid_reduce<1, BLAS_THREADS>(v1, ra, &st->ticket[4]);
+  } else {
+    grid_reduce<3, BLAS_THREADS>(red, ra, &st->ticket[4]);
+  }
+}
+
+// Mixed precision: x64 += x32, x32 = 0.
+__global__ void __launch_bounds__(BLAS_THREADS) accum_x_kernel(double2* __restrict__ x64, float2* __restrict__ x32, long long n) {
+  OK_GRID_STRIDE(i, n) {
+    float2 f = x32[i];
+    double2 d = x64[i];
+    d.x += (double)f.x;
+    d.y += (double)f.y;
+    x64[i] = d;
+    x32[i] = make_float2(0.f, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------- launchers
+static int g_sms = 0;
+
+int blas_blocks(long long units) {
+  if (g_sms == 0) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 132;
+    g_sms = sms;
+  }
+  long long need = (units + BLAS_THREADS - 1) / BLAS_THREADS;
+  long long cap = (long long)g_sms * 8;
+  return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
+template <typename R> long long units_of(long long ncomplex) { return ncomplex / Unit<R>::NC; }
+
+template <typename R>
+int launch_update_s(const cx<R>* r, const cx<R>* v, cx<R>* s, long long n, const SolverState* st, cudaStream_t strm) {
+  using T = typename Unit<R>::T;
+  long long nu = units_of<R>(n);
+  update_s_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((const T*)r, (const T*)v, (T*)s, nu, st);
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+template <typename R>
+int launch_update_xr(cx<R>* x, const cx<R>* p, const cx<R>* s, const cx<R>* t, cx<R>* r, const cx<R>* rhat, long long n,
+                     SolverState* st, double* part, cudaStream_t strm) {
+  using T = typename Unit<R>::T;
+  long long nu = units_of<R>(n);
+  RedArgs ra{st, part, nullptr, FIN_XR};
+  update_xr_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r,
+                                                                  (const T*)rhat, nu, st, ra);
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+template <typename R>
+int launch_update_p(cx<R>* p, const cx<R>* r, const cx<R>* v, long long n, const SolverState* st, cudaStream_t strm) {
+  using T = typename Unit<R>::T;
+  long long nu = units_of<R>(n);
+  update_p_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((T*)p, (const T*)r, (const T*)v, nu, st);
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+template <typename R>
+int launch_restart(const cx<R>* r, cx<R>* rhat, cx<R>* p, long long n, SolverState* st, double* part, cudaStream_t strm) {
+  using T = typename Unit<R>::T;
+  long long nu = units_of<R>(n);
+  RedArgs ra{st, part, nullptr, FIN_RESTART};
+  restart_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((const T*)r, (T*)rhat, (T*)p, nu, st, ra);
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+int launch_demote(const cx<double>* r64, cx<float>* r32, cx<float>* rhat, cx<float>* p, long long n, bool restart,
+                  SolverState* st, double* part, cudaStream_t strm) {
+  int nb = blas_blocks(n);
+  if (restart) {
+    RedArgs ra{st, part, nullptr, FIN_RESTART};
+    demote_kernel<true><<<nb, BLAS_THREADS, 0, strm>>>((const double2*)r64, (float2*)r32, (float2*)rhat, (float2*)p, n, st, ra);
+  } else {
+    RedArgs ra{st, part, nullptr, FIN_CONTINUE};
+    demote_kernel<false><<<nb, BLAS_THREADS, 0, strm>>>((const double2*)r64, (float2*)r32, (float2*)rhat, (float2*)p, n, st, ra);
+  }
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+int launch_accum_x(cx<double>* x64, cx<float>* x32, long long n, cudaStream_t strm) {
+  accum_x_kernel<<<blas_blocks(n), BLAS_THREADS, 0, strm>>>((double2*)x64, (float2*)x32, n);
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+template int launch_update_s<double>(const cx<double>*, const cx<double>*, cx<double>*, long long, const SolverState*, cudaStream_t);
+template int launch_update_s<float>(const cx<float>*, const cx<float>*, cx<float>*, long long, const SolverState*, cudaStream_t);
+template int launch_update_xr<double>(cx<double>*, const cx<double>*, const cx<double>*, const cx<double>*, cx<double>*, const cx<double>*, long long, SolverState*, double*, cudaStream_t);
+template int launch_update_xr<float>(cx<float>*, const cx<float>*, const cx<float>*, const cx<float>*, cx<float>*, const cx<float>*, long long, SolverState*, double*, cudaStream_t);
+template int launch_update_p<double>(cx<double>*, const cx<double>*, const cx<double>*, long long, const SolverState*, cudaStream_t);
+template int launch_update_p<float>(cx<float>*, const cx<float>*, const cx<float>*, long long, const SolverState*, cudaStream_t);
+template int launch_restart<double>(const cx<double>*, cx<double>*, cx<double>*, long long, SolverState*, double*, cudaStream_t);
+template int launch_restart<float>(const cx<float>*, cx<float>*, cx<float>*, long long, SolverState*, double*, cudaStream_t);
+
+}  // namespace okgb

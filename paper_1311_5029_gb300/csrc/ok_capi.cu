@@ -1,0 +1,122 @@
+// The extern "C" boundary declared in include/ok.h: argument checks, error codes, launch count.
+#include "ok_launch.cuh"
+
+#include <atomic>
+#include <cmath>
+
+namespace okgb {
+
+static std::atomic<unsigned long long> g_launches{0};
+static thread_local int g_last_cuda_error = 0;
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
+void set_cuda_error(cudaError_t e) { g_last_cuda_error = (int)e; }
+
+static bool coeffs_finite(const ok_coeffs* c) {
+  const double v[] = {c->u0, c->am0, c->kappa, c->zeta, c->r_s, c->c_B, c->c_E, c->c_EE, c->c1, c->c2, c->c3, c->c4, c->c5};
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
+}  // namespace okgb
+
+using namespace okgb;
+
+extern "C" {
+
+int ok_precompute_W(const ok_lattice* lat, const void* links, ok_prec links_prec, const ok_coeffs* coeffs, int W_precs,
+                    void* stream, ok_W** W_out) {
+  if (!coeffs || !okgb::coeffs_finite(coeffs)) return OK_EINVAL;
+  return precompute(lat, links, links_prec, coeffs, W_precs, (cudaStream_t)stream, W_out);
+}
+
+void ok_free_W(ok_W* W) {
+  if (!W) return;
+  if (W->W64) cudaFree(W->W64);
+  if (W->W32) cudaFree(W->W32);
+  delete W;
+}
+
+double ok_W_u0(const ok_W* W) { return W ? W->sc.u0 : NAN; }
+
+double ok_W_plaquette(const ok_W* W) { return W ? W->sc.plaq : NAN; }
+
+int ok_W_info(const ok_W* W, ok_lattice* lat, int* W_precs, size_t* bytes) {
+  if (!W) return OK_EINVAL;
+  if (lat) *lat = W->lat;
+  if (W_precs) *W_precs = W->precs;
+  if (bytes) *bytes = W->bytes;
+  return OK_SUCCESS;
+}
+
+int ok_apply_M(const ok_W* W, ok_prec prec, const void* psi, void* out, void* stream) {
+  if (!W || !psi || !out) return OK_EINVAL;
+  size_t es = prec == OK_F64 ? 16 : prec == OK_F32 ? 8 : 0;
+  if (es == 0) return OK_EINVAL;
+  size_t bytes = (size_t)W->g.V * 12 * es;
+  const char* a = (const char*)psi;
+  const char* b = (const char*)out;
+  if (a < b + bytes && b < a + bytes) return OK_EINVAL;  // overlapping ranges
+  if (((uintptr_t)psi | (uintptr_t)out) & 15) return OK_EINVAL;
+  if (prec == OK_F64) {
+    if (!W->W64) return OK_EINVAL;
+    EpiArgs<double> e{};
+    return launch_apply<double>(W, (const cx<double>*)psi, (cx<double>*)out, EPI_NONE, e, (cudaStream_t)stream);
+  }
+  if (!W->W32) return OK_EINVAL;
+  EpiArgs<float> e{};
+  return launch_apply<float>(W, (const cx<float>*)psi, (cx<float>*)out, EPI_NONE, e, (cudaStream_t)stream);
+}
+
+ok_solve_params ok_default_solve_params(double tol, int maxiter) {
+  ok_solve_params p;
+  p.tol = tol;
+  p.maxiter = maxiter;
+  p.mode = OK_SOLVE_AUTO;
+  p.delta = 0.1;
+  p.max_restarts = 5;
+  p.check_every = 8;
+  return p;
+}
+
+int ok_bicgstab_ex(const ok_W* W, const void* src, void* x, const ok_solve_params* params, ok_solve_info* info,
+                   void* stream) {
+  if (!W || !src || !x || !params) return OK_EINVAL;
+  if ((((uintptr_t)src) | ((uintptr_t)x)) & 15) return OK_EINVAL;
+  return bicgstab(W, (const cx<double>*)src, (cx<double>*)x, params, info, (cudaStream_t)stream);
+}
+
+int ok_bicgstab(const ok_W* W, const void* src, void* x, double tol, int maxiter, ok_solve_info* info, void* stream) {
+  ok_solve_params p = ok_default_solve_params(tol, maxiter);
+  return ok_bicgstab_ex(W, src, x, &p, info, stream);
+}
+
+int ok_true_residual(const ok_W* W, const void* b, const void* x, double* relres, void* stream) {
+  return true_residual(W, (const cx<double>*)b, (const cx<double>*)x, relres, (cudaStream_t)stream);
+}
+
+int ok_W_expand(const ok_W* W, ok_prec prec, int kind, void* out, void* stream) {
+  return expand(W, prec, kind, out, (cudaStream_t)stream);
+}
+
+unsigned long long ok_launch_count(void) { return launches(); }
+
+int ok_last_cuda_error(void) { return g_last_cuda_error; }
+
+const char* ok_strerror(int status) {
+  switch (status) {
+    case OK_SUCCESS: return "success";
+    case OK_EINVAL: return "invalid argument";
+    case OK_ENOMEM: return "out of memory";
+    case OK_ECUDA: return "CUDA error";
+    case OK_ENOCONV: return "solver did not converge";
+    case OK_EBREAKDOWN: return "BiCGStab breakdown";
+    case OK_ENONFINITE: return "non-finite value in the solver";
+    case OK_EINTERNAL: return "internal error";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

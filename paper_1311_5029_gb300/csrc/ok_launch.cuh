@@ -1,0 +1,53 @@
+// Declarations of the kernel launchers shared between translation units.
+#pragma once
+
+#include "ok_reduce.cuh"
+
+namespace okgb {
+
+// Fused epilogues of the apply kernel.
+enum : int {
+  EPI_NONE = 0,   // out = M psi
+  EPI_DOT = 1,    // out = M psi; reduce <rhat, out>
+  EPI_TS = 2,     // out = M psi; reduce <out, psi>, <out, out>
+  EPI_RESID = 3,  // out = b - M psi; reduce <out, out>, <b, b>
+};
+
+template <typename R> struct EpiArgs {
+  const cx<R>* rhat;   // EPI_DOT
+  const cx<R>* b;      // EPI_RESID
+  RedArgs ra;
+  unsigned* ticket;
+  const int* halt;     // if non-null and nonzero at launch, the kernel does nothing
+};
+
+template <typename R>
+int launch_apply(const ok_W* W, const cx<R>* psi, cx<R>* out, int epi, const EpiArgs<R>& ep, cudaStream_t st);
+int apply_blocks_needed(const ok_W* W);
+
+int blas_blocks(long long units);
+template <typename R>
+int launch_update_s(const cx<R>* r, const cx<R>* v, cx<R>* s, long long n, const SolverState* st, cudaStream_t strm);
+template <typename R>
+int launch_update_xr(cx<R>* x, const cx<R>* p, const cx<R>* s, const cx<R>* t, cx<R>* r, const cx<R>* rhat, long long n,
+                     SolverState* st, double* part, cudaStream_t strm);
+template <typename R>
+int launch_update_p(cx<R>* p, const cx<R>* r, const cx<R>* v, long long n, const SolverState* st, cudaStream_t strm);
+template <typename R>
+int launch_restart(const cx<R>* r, cx<R>* rhat, cx<R>* p, long long n, SolverState* st, double* part, cudaStream_t strm);
+int launch_demote(const cx<double>* r64, cx<float>* r32, cx<float>* rhat, cx<float>* p, long long n, bool restart,
+                  SolverState* st, double* part, cudaStream_t strm);
+int launch_accum_x(cx<double>* x64, cx<float>* x32, long long n, cudaStream_t strm);
+
+// ok_precompute.cu
+int geom_from_lattice(const ok_lattice* lat, Geom* g);
+int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, const ok_coeffs* c, int precs,
+               cudaStream_t st, ok_W** W_out);
+int expand(const ok_W* W, ok_prec prec, int kind, void* out, cudaStream_t st);
+
+// ok_solver.cu
+int bicgstab(const ok_W* W, const cx<double>* b, cx<double>* x, const ok_solve_params* prm, ok_solve_info* info,
+             cudaStream_t st);
+int true_residual(const ok_W* W, const cx<double>* b, const cx<double>* x, double* relres, cudaStream_t st);
+
+}  // namespace okgb

@@ -1,0 +1,582 @@
+// Precalculation of the W matrices (Sec. 2.2 "Precalculation"; Eqs. shifted_W_first ..
+// shifted_W_last): mean plaquette and tadpole factor u0, clover fields E_i and B_i, and the
+// forward set of W matrices per site in the site-blocked layout of ok_internal.cuh.
+//
+// Stored representation (NMAT = 43 colour matrices per site, all arithmetic FP64):
+//   The apply works in the basis h+- = psi_upper +- psi_lower of the two 2-spin halves, in which
+//   every hop except W^0 and W^+-_4 is block diagonal (W^+_i = [[D, S], [S, D]] acts as D + S on
+//   h+ and D - S on h-).  So the stored matrices are:
+//   * W^0 = u0/(2 kappa) + [[D0, S0], [-S0, D0]]: the 2x2 spin blocks of Y+- = (D0 +- i S0) / 4,
+//     which act on u -+ i l; the constant u0/(2 kappa)/4 is added to the diagonal blocks on the
+//     fly.  D0 = sum_k sigma_k d_k, S0 = sum_k sigma_k s_k, so each Y is [[y3, y1 - i y2],
+//     [y1 + i y2, -y3]]: 3 matrices per sign.                                    (6 matrices)
+//   * W^+_4 = [[0, S4], [S4, -U4]]: U4 / 2 and the blocks of S4 / 2.                 (4)
+//   * W^+_i: the four 2x2 spin blocks of (D^+_i + S^+_i) / 2 and of (D^+_i - S^+_i) / 2. (24)
+//   * W^{++}_ii = [[a V, b sigma_i V], [b sigma_i V, a V]]: V = U_i(x) U_i(x+i).       (3)
+//   * W^{++}_ij, W^{+-}_ij = [[0, S], [S, 0]] with S = c2/(2 u0) (sigma_i +- sigma_j) X:
+//     the colour part X times c2 / (4 u0).                                             (6)
+//   The backward matrices come from these at the neighbouring site by Eqs. conjugate and
+//   opp_diag_pre_mat inside the apply.
+#include "ok_launch.cuh"
+#include <new>
+
+namespace okgb {
+
+// ---------------------------------------------------------------------------- indexing
+__device__ __forceinline__ int wrapi(int x, int L) {
+  int r = x % L;
+  return r < 0 ? r + L : r;
+}
+
+struct Site {
+  int c[4];
+};
+
+__device__ __forceinline__ Site site_coords(int s, const Geom& g) {
+  Site p;
+  p.c[0] = s % g.L[0]; s /= g.L[0];
+  p.c[1] = s % g.L[1]; s /= g.L[1];
+  p.c[2] = s % g.L[2]; s /= g.L[2];
+  p.c[3] = s;
+  return p;
+}
+
+// Site index of x + (d0, d1, d2, d3) with periodic wrapping (gauge fields are periodic).
+__device__ __forceinline__ int nbr(const Site& p, const Geom& g, int d0, int d1, int d2, int d3) {
+  int x = wrapi(p.c[0] + d0, g.L[0]);
+  int y = wrapi(p.c[1] + d1, g.L[1]);
+  int z = wrapi(p.c[2] + d2, g.L[2]);
+  int t = wrapi(p.c[3] + d3, g.L[3]);
+  return x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
+}
+
+__device__ __forceinline__ int nbr_dir(const Site& p, const Geom& g, int mu, int n, int nu = 0, int m = 0) {
+  int d[4] = {0, 0, 0, 0};
+  d[mu] += n;
+  d[nu] += m;
+  return nbr(p, g, d[0], d[1], d[2], d[3]);
+}
+
+template <typename LT>
+__device__ __forceinline__ M3<double> load_link(const cx<LT>* __restrict__ U, int site, int mu) {
+  M3<double> m;
+  const cx<LT>* p = U + ((size_t)site * 4 + mu) * 9;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    cx<LT> v = p[k];
+    m.e[k] = mk<double>((double)v.re, (double)v.im);
+  }
+  return m;
+}
+
+__device__ __forceinline__ M3<double> load_eb(const cx<double>* __restrict__ EB, int site, int k) {
+  M3<double> m;
+  const cx<double>* p = EB + ((size_t)site * 6 + k) * 9;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) m.e[e] = p[e];
+  return m;
+}
+
+// ---------------------------------------------------------------------------- block reduction
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < THREADS / 32; ++i) r += sh[i];
+  }
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------- K1: clover + plaquette
+// F_{mu nu} = (Q - Q^dagger) / 8 with Q the four plaquette leaves around x traversed mu-then-nu;
+// E_i = F_{t i}, B_i = eps_ijk F_jk / 2.  The plaquette leaf U_mu(x) U_nu(x+mu) U_mu^dag(x+nu)
+// U_nu^dag(x) also feeds the mean plaquette.
+constexpr int K1_THREADS = 128;
+
+template <typename LT>
+__global__ void __launch_bounds__(K1_THREADS) clover_kernel(const cx<LT>* __restrict__ U, Geom g,
+                                                            cx<double>* __restrict__ EB,
+                                                            double* __restrict__ plaq_part) {
+  __shared__ double sh[K1_THREADS / 32];
+  int s = blockIdx.x * K1_THREADS + threadIdx.x;
+  double retr = 0.0;
+  if (s < g.V) {
+    Site p = site_coords(s, g);
+    M3<double> F[4][4];
+    for (int mu = 0; mu < 4; ++mu) {
+      for (int nu = mu + 1; nu < 4; ++nu) {
+        M3<double> Umx = load_link(U, s, mu), Unx = load_link(U, s, nu);
+        // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+        M3<double> l1 = m_mul(m_mul(Umx, load_link(U, nbr_dir(p, g, mu, 1), nu)),
+                              m_mul(m_dag(load_link(U, nbr_dir(p, g, nu, 1), mu)), m_dag(Unx)));
+        // leaf 2: U_nu(x) U_mu(x+nu-mu)^dag U_nu(x-mu)^dag U_mu(x-mu)
+        M3<double> l2 = m_mul(m_mul(Unx, m_dag(load_link(U, nbr_dir(p, g, nu, 1, mu, -1), mu))),
+                              m_mul(m_dag(load_link(U, nbr_dir(p, g, mu, -1), nu)),
+                                    load_link(U, nbr_dir(p, g, mu, -1), mu)));
+        // leaf 3: U_mu(x-mu)^dag U_nu(x-mu-nu)^dag U_mu(x-mu-nu) U_nu(x-nu)
+        M3<double> l3 = m_mul(m_mul(m_dag(load_link(U, nbr_dir(p, g, mu, -1), mu)),
+                                    m_dag(load_link(U, nbr_dir(p, g, mu, -1, nu, -1), nu))),
+                              m_mul(load_link(U, nbr_dir(p, g, mu, -1, nu, -1), mu),
+                                    load_link(U, nbr_dir(p, g, nu, -1), nu)));
+        // leaf 4: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^dag
+        M3<double> l4 = m_mul(m_mul(m_dag(load_link(U, nbr_dir(p, g, nu, -1), nu)),
+                                    load_link(U, nbr_dir(p, g, nu, -1), mu)),
+                              m_mul(load_link(U, nbr_dir(p, g, nu, -1, mu, 1), nu), m_dag(Umx)));
+        retr += l1.e[0].re + l1.e[4].re + l1.e[8].re;
+        M3<double> Q = m_add(m_add(l1, l2), m_add(l3, l4));
+        M3<double> f = m_rscale(0.125, m_sub(Q, m_dag(Q)));
+        F[mu][nu] = f;
+        F[nu][mu] = m_rscale(-1.0, f);
+      }
+    }
+    cx<double>* out = EB + (size_t)s * 6 * 9;
+    for (int i = 0; i < 3; ++i) {
+      const M3<double>& E = F[3][i];
+      const M3<double>& B = F[(i + 1) % 3][(i + 2) % 3];
+      for (int e = 0; e < 9; ++e) {
+        out[i * 9 + e] = E.e[e];
+        out[(3 + i) * 9 + e] = B.e[e];
+      }
+    }
+  }
+  double tot = block_sum<K1_THREADS>(retr, sh);
+  if (threadIdx.x == 0) plaq_part[blockIdx.x] = tot;
+}
+
+// Sum the per-block plaquette partials in a fixed order; derive u0 and the stored scalars.
+__global__ void scalars_kernel(const double* __restrict__ plaq_part, int nparts, Geom g, ok_coeffs c,
+                               WScalars* __restrict__ out) {
+  __shared__ double sh[32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += plaq_part[i];
+  // fixed-shape tree over the 32 lanes of each warp, then warps in order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+    WScalars s;
+    s.plaq = tot / (18.0 * (double)g.V);
+    s.u0 = c.u0 > 0.0 ? c.u0 : pow(s.plaq, 0.25);
+    s.inv2kappa = c.kappa > 0.0 ? 1.0 / (2.0 * c.kappa) : c.am0 + 1.0 + 3.0 * c.r_s * c.zeta + 18.0 * c.c4;
+    s.c0q = 0.25 * s.u0 * s.inv2kappa;
+    s.a_ii = c.c4 / (2.0 * s.u0);
+    s.b_ii = (c.c1 + 2.0 * c.c2) / (4.0 * s.u0);
+    *out = s;
+  }
+}
+
+// ---------------------------------------------------------------------------- K2: W matrices
+struct WOut {
+  cx<double>* W64;
+  cx<float>* W32;
+};
+
+__device__ __forceinline__ void store_mat(const WOut& o, int site, int m, const M3<double>& a) {
+  size_t blk = (size_t)(site >> 5);
+  int lane = site & 31;
+  size_t base = (blk * NMAT + m) * 9 * LANES + lane;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    if (o.W64) o.W64[base + (size_t)e * LANES] = a.e[e];
+    if (o.W32) o.W32[base + (size_t)e * LANES] = mk<float>((float)a.e[e].re, (float)a.e[e].im);
+  }
+}
+
+__device__ __forceinline__ int levi(int i, int j, int k) {
+  if (i == j || j == k || i == k) return 0;
+  return ((j - i + 3) % 3 == 1) ? 1 : -1;
+}
+
+constexpr int K2_THREADS = 64;
+
+// part 0: W^0 and W^+_4; parts 1..3: W^+_i for i = part - 1; part 4: W^{++}_ii, W^{++}_ij, W^{+-}_ij.
+template <typename LT>
+__global__ void __launch_bounds__(K2_THREADS) w_kernel(const cx<LT>* __restrict__ U,
+                                                       const cx<double>* __restrict__ EB, Geom g,
+                                                       ok_coeffs c, const WScalars* __restrict__ scp,
+                                                       WOut o, int part) {
+  int s = blockIdx.x * K2_THREADS + threadIdx.x;
+  if (s >= g.V) return;
+  const WScalars sc = *scp;
+  const double u0 = sc.u0;
+  const double u03 = u0 * u0 * u0, u04 = u03 * u0;
+  Site p = site_coords(s, g);
+  const cx<double> I = mk<double>(0.0, 1.0);
+
+  if (part == 0) {
+    // W^0: D0 = -(c_B zeta + 16 c5)/(2 u0^3) i sum sigma_k B_k, S0 = -(c_E zeta)/(2 u0^3) sum sigma_k E_k
+    const double cd = -(c.c_B * c.zeta + 16.0 * c.c5) / (2.0 * u03);
+    const double cs = -(c.c_E * c.zeta) / (2.0 * u03);
+    M3<double> yp[3], ym[3];
+    for (int k = 0; k < 3; ++k) {
+      M3<double> d = m_scale(mk<double>(0.0, cd), load_eb(EB, s, 3 + k));   // i cd B_k
+      M3<double> e = m_rscale(cs, load_eb(EB, s, k));                      // cs E_k
+      M3<double> ie = m_scale(I, e);
+      yp[k] = m_rscale(0.25, m_add(d, ie));
+      ym[k] = m_rscale(0.25, m_sub(d, ie));
+    }
+    // [[y_z, y_x - i y_y], [y_x + i y_y, -y_z]]
+    store_mat(o, s, M_Y0P + 0, yp[2]);
+    store_mat(o, s, M_Y0P + 1, m_sub(yp[0], m_scale(I, yp[1])));
+    store_mat(o, s, M_Y0P + 2, m_add(yp[0], m_scale(I, yp[1])));
+    store_mat(o, s, M_Y0M + 0, ym[2]);
+    store_mat(o, s, M_Y0M + 1, m_sub(ym[0], m_scale(I, ym[1])));
+    store_mat(o, s, M_Y0M + 2, m_add(ym[0], m_scale(I, ym[1])));
+    // W^+_4: S4 = c_EE/(2 u0^4) (U_t E(x+t) - E(x) U_t), sum over sigma_k
+    M3<double> Ut = load_link(U, s, 3);
+    int st = nbr_dir(p, g, 3, 1);
+    const double ct = c.c_EE / (2.0 * u04);
+    M3<double> tk[3];
+    for (int k = 0; k < 3; ++k)
+      tk[k] = m_rscale(0.5 * ct, m_sub(m_mul(Ut, load_eb(EB, st, k)), m_mul(load_eb(EB, s, k), Ut)));
+    store_mat(o, s, M_UT, m_rscale(0.5, Ut));
+    store_mat(o, s, M_ST + 0, tk[2]);
+    store_mat(o, s, M_ST + 1, m_sub(tk[0], m_scale(I, tk[1])));
+    store_mat(o, s, M_ST + 2, m_add(tk[0], m_scale(I, tk[1])));
+    return;
+  }
+
+  if (part >= 1 && part <= 3) {
+    const int i = part - 1;
+    M3<double> Ui = load_link(U, s, i);
+    int si = nbr_dir(p, g, i, 1);
+    M3<double> Bx[3], Bxi[3];
+    for (int k = 0; k < 3; ++k) {
+      Bx[k] = load_eb(EB, s, 3 + k);
+      Bxi[k] = load_eb(EB, si, 3 + k);
+    }
+    // S^+_i = 1 (x) b0 + sum_l sigma_l (x) b_l
+    const double c3f = c.c3 / (2.0 * u04);
+    M3<double> b[4];
+    b[0] = m_scale(mk<double>(0.0, c3f), m_add(m_mul(Ui, Bxi[i]), m_mul(Bx[i], Ui)));
+    for (int l = 0; l < 3; ++l) {
+      M3<double> acc = (l == i) ? m_rscale(0.5 * (c.zeta - 2.0 * c.c1 - 12.0 * c.c2), Ui) : m_zero<double>();
+      for (int k = 0; k < 3; ++k) {
+        int e = levi(i, k, l);
+        if (e == 0) continue;
+        acc = m_sub(acc, m_rscale(c3f * e, m_sub(m_mul(Ui, Bxi[k]), m_mul(Bx[k], Ui))));
+      }
+      b[1 + l] = acc;
+    }
+    // D^+_i = 1 (x) a0 + sum_l sigma_l (x) a_l
+    M3<double> a[4];
+    a[0] = m_rscale(-0.5 * (c.r_s * c.zeta + 8.0 * c.c4), Ui);
+    const double cst = 0.25 * c.c5 * (1.0 / (u0 * u0) - 1.0 / u04);
+    const double c5f = c.c5 / u04;
+    M3<double> staple[3];
+    for (int k = 0; k < 3; ++k) {
+      if (k == i) { staple[k] = m_zero<double>(); continue; }
+      // U_k(x) U_i(x+k) U_k(x+i)^dag - U_k(x-k)^dag U_i(x-k) U_k(x-k+i)
+      M3<double> up = m_mul(m_mul(load_link(U, s, k), load_link(U, nbr_dir(p, g, k, 1), i)),
+                            m_dag(load_link(U, si, k)));
+      int smk = nbr_dir(p, g, k, -1);
+      M3<double> dn = m_mul(m_mul(m_dag(load_link(U, smk, k)), load_link(U, smk, i)),
+                            load_link(U, nbr_dir(p, g, k, -1, i, 1), k));
+      staple[k] = m_sub(up, dn);
+    }
+    for (int l = 0; l < 3; ++l) {
+      M3<double> acc = m_zero<double>();
+      for (int k = 0; k < 3; ++k) {
+        int e = levi(i, l, k);
+        if (e == 0) continue;
+        acc = m_add(acc, m_scale(mk<double>(0.0, cst * e), staple[k]));
+      }
+      if (l != i) acc = m_add(acc, m_scale(mk<double>(0.0, c5f), m_add(m_mul(Ui, Bxi[l]), m_mul(Bx[l], Ui))));
+      a[1 + l] = acc;
+    }
+    // blocks of (D +- S)/2: 00 = q0 + q3, 01 = q1 - i q2, 10 = q1 + i q2, 11 = q0 - q3
+    for (int sg = 0; sg < 2; ++sg) {
+      M3<double> q[4];
+      for (int k = 0; k < 4; ++k) q[k] = m_rscale(0.5, sg == 0 ? m_add(a[k], b[k]) : m_sub(a[k], b[k]));
+      int base = M_WP + 8 * i + 4 * sg;
+      store_mat(o, s, base + 0, m_add(q[0], q[3]));
+      store_mat(o, s, base + 1, m_sub(q[1], m_scale(I, q[2])));
+      store_mat(o, s, base + 2, m_add(q[1], m_scale(I, q[2])));
+      store_mat(o, s, base + 3, m_sub(q[0], q[3]));
+    }
+    return;
+  }
+
+  // part 4: two-hop colour matrices
+  M3<double> Ul[3];
+  for (int i = 0; i < 3; ++i) Ul[i] = load_link(U, s, i);
+  for (int i = 0; i < 3; ++i) store_mat(o, s, M_VII + i, m_mul(Ul[i], load_link(U, nbr_dir(p, g, i, 1), i)));
+  const double cij = c.c2 / (4.0 * u0);
+  int pr = 0;
+  for (int i = 0; i < 3; ++i) {
+    for (int j = i + 1; j < 3; ++j, ++pr) {
+      // U_i(x) U_j(x+i) + U_j(x) U_i(x+j)
+      M3<double> v = m_add(m_mul(Ul[i], load_link(U, nbr_dir(p, g, i, 1), j)),
+                           m_mul(Ul[j], load_link(U, nbr_dir(p, g, j, 1), i)));
+      store_mat(o, s, M_VIJ + pr, m_rscale(cij, v));
+      // U_i(x) U_j(x-j+i)^dag + U_j(x-j)^dag U_i(x-j)
+      int smj = nbr_dir(p, g, j, -1);
+      M3<double> x = m_add(m_mul(Ul[i], m_dag(load_link(U, nbr_dir(p, g, j, -1, i, 1), j))),
+                           m_mul(m_dag(load_link(U, smj, j)), load_link(U, smj, i)));
+      store_mat(o, s, M_XIJ + pr, m_rscale(cij, x));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------- expand (inspection)
+template <typename R>
+__device__ __forceinline__ M3<double> fetch(const cx<R>* __restrict__ W, int site, int m) {
+  size_t blk = (size_t)(site >> 5);
+  int lane = site & 31;
+  size_t base = (blk * NMAT + m) * 9 * LANES + lane;
+  M3<double> a;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    cx<R> v = W[base + (size_t)e * LANES];
+    a.e[e] = mk<double>((double)v.re, (double)v.im);
+  }
+  return a;
+}
+
+// out[(3 * (2 * tr + sr) + cr) * 12 + 3 * (2 * tc + sc) + cc] for spin block (tr, tc) and
+// inner 2x2 spin entry (sr, sc).
+__device__ __forceinline__ void put(cx<double>* o, int tr, int tc, int sr, int sc, const M3<double>& a, cx<double> f) {
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) {
+      cx<double>& d = o[(3 * (2 * tr + sr) + r) * 12 + 3 * (2 * tc + sc) + q];
+      d = d + f * a.e[3 * r + q];
+    }
+}
+
+// Add the 6x6 matrix sum_{sr,sc} blk[sr][sc] (x) colour into spin block (tr, tc) times f.
+__device__ __forceinline__ void put6(cx<double>* o, int tr, int tc, const M3<double> b[4], cx<double> f) {
+  put(o, tr, tc, 0, 0, b[0], f);
+  put(o, tr, tc, 0, 1, b[1], f);
+  put(o, tr, tc, 1, 0, b[2], f);
+  put(o, tr, tc, 1, 1, b[3], f);
+}
+
+// 2x2 Pauli matrix entries sigma_k[r][c] as complex.
+__device__ __forceinline__ cx<double> pauli(int k, int r, int c) {
+  if (k == 0) return mk<double>(r != c ? 1.0 : 0.0, 0.0);
+  if (k == 1) return r == c ? mk<double>(0.0, 0.0) : mk<double>(0.0, r == 0 ? -1.0 : 1.0);
+  return r != c ? mk<double>(0.0, 0.0) : mk<double>(r == 0 ? 1.0 : -1.0, 0.0);
+}
+
+template <typename R>
+__global__ void expand_kernel(const cx<R>* __restrict__ W, Geom g, const WScalars* __restrict__ scp, int kind,
+                              cx<double>* __restrict__ out) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const WScalars sc = *scp;
+  cx<double>* o = out + (size_t)s * 144;
+  for (int k = 0; k < 144; ++k) o[k] = mk<double>(0.0, 0.0);
+  const cx<double> one = mk<double>(1.0, 0.0);
+  const cx<double> I = mk<double>(0.0, 1.0);
+  if (kind == 0) {
+    M3<double> yp[4], ym[4];
+    M3<double> c0 = m_rscale(sc.c0q, m_eye<double>());
+    M3<double> a0 = fetch(W, s, M_Y0P), a1 = fetch(W, s, M_Y0P + 1), a2 = fetch(W, s, M_Y0P + 2);
+    yp[0] = m_add(a0, c0); yp[1] = a1; yp[2] = a2; yp[3] = m_sub(c0, a0);
+    M3<double> b0 = fetch(W, s, M_Y0M), b1 = fetch(W, s, M_Y0M + 1), b2 = fetch(W, s, M_Y0M + 2);
+    ym[0] = m_add(b0, c0); ym[1] = b1; ym[2] = b2; ym[3] = m_sub(c0, b0);
+    // W0 = [[D', S], [-S, D']] with D' = 2 (Y+ + Y-), S = -2 i (Y+ - Y-)
+    const cx<double> two = mk<double>(2.0, 0.0), m2i = mk<double>(0.0, -2.0), p2i = mk<double>(0.0, 2.0);
+    for (int tt = 0; tt < 2; ++tt) {
+      put6(o, tt, tt, yp, two);
+      put6(o, tt, tt, ym, two);
+    }
+    put6(o, 0, 1, yp, m2i); put6(o, 0, 1, ym, p2i);
+    put6(o, 1, 0, yp, p2i); put6(o, 1, 0, ym, m2i);
+    return;
+  }
+  if (kind >= 1 && kind <= 3) {
+    int i = kind - 1;
+    M3<double> pp[4], pm[4];
+    for (int k = 0; k < 4; ++k) { pp[k] = fetch(W, s, M_WP + 8 * i + k); pm[k] = fetch(W, s, M_WP + 8 * i + 4 + k); }
+    // D = P+ + P-, S = P+ - P- (stored halves)
+    const cx<double> mone = mk<double>(-1.0, 0.0);
+    for (int tr = 0; tr < 2; ++tr)
+      for (int tc = 0; tc < 2; ++tc) {
+        put6(o, tr, tc, pp, one);
+        put6(o, tr, tc, pm, tr == tc ? one : mone);
+      }
+    return;
+  }
+  if (kind == 4) {
+    M3<double> Uh = fetch(W, s, M_UT);
+    M3<double> t0 = fetch(W, s, M_ST), t1 = fetch(W, s, M_ST + 1), t2 = fetch(W, s, M_ST + 2);
+    M3<double> S[4] = {t0, t1, t2, m_rscale(-1.0, t0)};
+    const cx<double> two = mk<double>(2.0, 0.0);
+    put6(o, 0, 1, S, two);
+    put6(o, 1, 0, S, two);
+    put(o, 1, 1, 0, 0, Uh, mk<double>(-2.0, 0.0));
+    put(o, 1, 1, 1, 1, Uh, mk<double>(-2.0, 0.0));
+    return;
+  }
+  if (kind >= 5 && kind <= 7) {
+    int i = kind - 5;
+    M3<double> V = fetch(W, s, M_VII + i);
+    for (int tr = 0; tr < 2; ++tr)
+      for (int tc = 0; tc < 2; ++tc)
+        for (int sr = 0; sr < 2; ++sr)
+          for (int scc = 0; scc < 2; ++scc) {
+            // [[D, S], [S, D]], D = 2 a (1 (x) V), S = 2 b (sigma_i (x) V)
+            cx<double> f = mk<double>(0.0, 0.0);
+            if (tr == tc && sr == scc) f = mk<double>(2.0 * sc.a_ii, 0.0);
+            if (tr != tc) f = (2.0 * sc.b_ii) * pauli(i, sr, scc);
+            if (f.re != 0.0 || f.im != 0.0) put(o, tr, tc, sr, scc, V, f);
+          }
+    return;
+  }
+  if (kind >= 8 && kind <= 13) {
+    int pr = (kind - 8) % 3;
+    int i = pr == 2 ? 1 : 0;
+    int j = pr == 0 ? 1 : 2;
+    bool plus = kind <= 10;
+    M3<double> X = fetch(W, s, (plus ? M_VIJ : M_XIJ) + pr);
+    for (int sr = 0; sr < 2; ++sr)
+      for (int scc = 0; scc < 2; ++scc) {
+        cx<double> f = pauli(i, sr, scc) + (plus ? one : mk<double>(-1.0, 0.0)) * pauli(j, sr, scc);
+        f = 2.0 * f;
+        if (f.re != 0.0 || f.im != 0.0) {
+          put(o, 0, 1, sr, scc, X, f);
+          put(o, 1, 0, sr, scc, X, f);
+        }
+      }
+    return;
+  }
+  (void)I;
+}
+
+// ---------------------------------------------------------------------------- host side
+static int check_lattice(const ok_lattice* lat, Geom* g) {
+  if (!lat) return OK_EINVAL;
+  long long V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (lat->dims[mu] < 1 || lat->dims[mu] > OK_MAX_SITES) return OK_EINVAL;
+    if (lat->bc[mu] != 1 && lat->bc[mu] != -1) return OK_EINVAL;
+    V *= lat->dims[mu];
+    if (V > OK_MAX_SITES) return OK_EINVAL;
+  }
+  g->bcneg = 0;
+  for (int mu = 0; mu < 4; ++mu) {
+    g->L[mu] = lat->dims[mu];
+    if (lat->bc[mu] == -1) g->bcneg |= 1 << mu;
+  }
+  g->V = (int)V;
+  g->nblk = (int)((V + LANES - 1) / LANES);
+  return OK_SUCCESS;
+}
+
+int geom_from_lattice(const ok_lattice* lat, Geom* g) { return check_lattice(lat, g); }
+
+template <typename LT>
+static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaStream_t st,
+                          cx<double>* EB, double* part, WScalars* dsc) {
+  const Geom& g = W->g;
+  const cx<LT>* U = (const cx<LT>*)links;
+  int nb1 = grid_for(g.V, K1_THREADS);
+  clover_kernel<LT><<<nb1, K1_THREADS, 0, st>>>(U, g, EB, part);
+  OK_LAUNCH_CHECK();
+  scalars_kernel<<<1, 256, 0, st>>>(part, nb1, g, *c, dsc);
+  OK_LAUNCH_CHECK();
+  WOut o{(cx<double>*)W->W64, (cx<float>*)W->W32};
+  int nb2 = grid_for(g.V, K2_THREADS);
+  for (int part_id = 0; part_id < 5; ++part_id) {
+    w_kernel<LT><<<nb2, K2_THREADS, 0, st>>>(U, EB, g, *c, dsc, o, part_id);
+    OK_LAUNCH_CHECK();
+  }
+  return OK_SUCCESS;
+}
+
+int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, const ok_coeffs* c,
+               int precs, cudaStream_t st, ok_W** W_out) {
+  if (!lat || !links || !c || !W_out) return OK_EINVAL;
+  if (links_prec != OK_F64 && links_prec != OK_F32) return OK_EINVAL;
+  if (precs <= 0 || (precs & ~(OK_W_F64 | OK_W_F32))) return OK_EINVAL;
+  if (!(c->u0 > 0.0) && c->u0 > 0.0) return OK_EINVAL;
+  *W_out = nullptr;
+  Geom g;
+  if (check_lattice(lat, &g) != OK_SUCCESS) return OK_EINVAL;
+  ok_W* W = new (std::nothrow) ok_W();
+  if (!W) return OK_ENOMEM;
+  W->g = g;
+  W->lat = *lat;
+  W->precs = precs;
+  OK_CUDA_TRY(cudaGetDevice(&W->device));
+  size_t elems = (size_t)g.nblk * SITE_ELEMS * LANES;
+  int rc = OK_SUCCESS;
+  cx<double>* EB = nullptr;
+  double* part = nullptr;
+  WScalars* dsc = nullptr;
+  auto fail = [&](int code) {
+    if (EB) cudaFree(EB);
+    if (part) cudaFree(part);
+    if (dsc) cudaFree(dsc);
+    if (W->W64) cudaFree(W->W64);
+    if (W->W32) cudaFree(W->W32);
+    delete W;
+    return code;
+  };
+  cudaError_t e;
+  if (precs & OK_W_F64) {
+    e = cudaMalloc(&W->W64, elems * sizeof(cx<double>));
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
+    e = cudaMemsetAsync(W->W64, 0, elems * sizeof(cx<double>), st);
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
+  }
+  if (precs & OK_W_F32) {
+    e = cudaMalloc(&W->W32, elems * sizeof(cx<float>));
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
+    e = cudaMemsetAsync(W->W32, 0, elems * sizeof(cx<float>), st);
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
+  }
+  W->bytes = (W->W64 ? elems * sizeof(cx<double>) : 0) + (W->W32 ? elems * sizeof(cx<float>) : 0);
+  int nb1 = grid_for(g.V, K1_THREADS);
+  e = cudaMalloc(&EB, (size_t)g.V * 6 * 9 * sizeof(cx<double>));
+  if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
+  e = cudaMalloc(&part, (size_t)nb1 * sizeof(double));
+  if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
+  e = cudaMalloc(&dsc, sizeof(WScalars));
+  if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
+  rc = links_prec == OK_F64 ? run_precompute<double>(W, links, c, st, EB, part, dsc)
+                            : run_precompute<float>(W, links, c, st, EB, part, dsc);
+  if (rc != OK_SUCCESS) return fail(rc);
+  e = cudaMemcpyAsync(&W->sc, dsc, sizeof(WScalars), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
+  cudaFree(EB);
+  cudaFree(part);
+  cudaFree(dsc);
+  EB = nullptr; part = nullptr; dsc = nullptr;
+  *W_out = W;
+  return OK_SUCCESS;
+}
+
+int expand(const ok_W* W, ok_prec prec, int kind, void* out, cudaStream_t st) {
+  if (!W || !out || kind < 0 || kind > 13) return OK_EINVAL;
+  const void* src = prec == OK_F64 ? W->W64 : prec == OK_F32 ? W->W32 : nullptr;
+  if (!src) return OK_EINVAL;
+  WScalars* dsc = nullptr;
+  OK_CUDA_TRY(cudaMallocAsync((void**)&dsc, sizeof(WScalars), st));
+  cudaError_t e = cudaMemcpyAsync(dsc, &W->sc, sizeof(WScalars), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) { cudaFreeAsync(dsc, st); set_cuda_error(e); return OK_ECUDA; }
+  int nb = grid_for(W->g.V, 64);
+  if (prec == OK_F64)
+    expand_kernel<double><<<nb, 64, 0, st>>>((const cx<double>*)src, W->g, dsc, kind, (cx<double>*)out);
+  else
+    expand_kernel<float><<<nb, 64, 0, st>>>((const cx<float>*)src, W->g, dsc, kind, (cx<double>*)out);
+  count_launch();
+  e = cudaGetLastError();
+  cudaError_t e2 = cudaFreeAsync(dsc, st);
+  if (e != cudaSuccess || e2 != cudaSuccess) { set_cuda_error(e != cudaSuccess ? e : e2); return OK_ECUDA; }
+  return OK_SUCCESS;
+}
+
+}  // namespace okgb

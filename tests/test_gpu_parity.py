@@ -1,0 +1,174 @@
+"""GPU parity of the precompute (A0-A2) and the apply (A3) against the oracle, through the C ABI.
+
+Tolerances (the operator's own bar): FP64 1e-12 relative, FP32 1e-5 relative.  W matrices are
+compared element by element with every one of the 14 stored forward kinds reconstructed by
+ok_W_expand; applies are compared on whole fields at small sizes and on sampled sites at the
+16^3 x 32 and 28^3 x 96 sizes."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import wform, direct, gauge
+from tests.gpu_common import SMALL_CASES, CASE_IDS, to_dev, rel_l2, rel_max
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+ok = pytest.importorskip("paper_1311_5029_gb300")
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    ok.load()
+    yield
+
+
+@pytest.mark.parametrize("case", SMALL_CASES, ids=CASE_IDS)
+def test_plaquette_and_u0(case):
+    _, dims, bc, eps, c = case
+    U = synth.random_links(dims, eps, 1000 + sum(dims))
+    W = ok.precompute_W(to_dev(U), c, bc, ok.W_F64)
+    assert abs(W.plaquette - gauge.mean_plaquette(U)) < 1e-13
+    u0 = c.u0 if c.u0 > 0 else gauge.tadpole_u0(U)
+    assert abs(W.u0 - u0) < 1e-13
+
+
+@pytest.mark.parametrize("case", SMALL_CASES, ids=CASE_IDS)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_stored_W_matches_paper_formulas(case, prec):
+    _, dims, bc, eps, c = case
+    U = synth.random_links(dims, eps, 2000 + sum(dims))
+    W = ok.precompute_W(to_dev(U), c, bc, ok.W_F64 | ok.W_F32)
+    ref = wform.forward_set(U, c)
+    V = int(np.prod(dims))
+    tol = FP64_TOL if prec == "f64" else 2e-6
+    for kind, name in enumerate(ok.W_KINDS):
+        got = ok.W_expand(W, kind, ok.F64 if prec == "f64" else ok.F32).cpu().numpy()
+        exp = ref[name].reshape(V, 12, 12)
+        assert rel_max(got, exp) < tol, (name, rel_max(got, exp))
+
+
+@pytest.mark.parametrize("case", SMALL_CASES, ids=CASE_IDS)
+def test_apply_fp64(case):
+    _, dims, bc, eps, c = case
+    U = synth.random_links(dims, eps, 3000 + sum(dims))
+    psi = synth.gaussian_source(dims, 3100 + sum(dims))
+    W = ok.precompute_W(to_dev(U), c, bc, ok.W_F64)
+    got = ok.apply_M(W, to_dev(psi)).cpu().numpy()
+    exp = wform.apply(U, c, psi, bc)
+    assert rel_l2(got, exp) < FP64_TOL
+    assert rel_max(got, exp) < 10 * FP64_TOL
+
+
+@pytest.mark.parametrize("case", SMALL_CASES, ids=CASE_IDS)
+def test_apply_fp32(case):
+    _, dims, bc, eps, c = case
+    U = synth.random_links(dims, eps, 4000 + sum(dims))
+    psi = synth.gaussian_source(dims, 4100 + sum(dims)).astype(np.complex64)
+    W = ok.precompute_W(to_dev(U), c, bc, ok.W_F32)
+    got = ok.apply_M(W, to_dev(psi)).cpu().numpy()
+    exp = wform.apply(U, c, psi.astype(np.complex128), bc)
+    assert rel_l2(got, exp) < FP32_TOL
+
+
+def test_links_in_fp32():
+    """complex64 links: the precompute widens them to FP64; the oracle gets the same rounded links."""
+    dims, bc = (5, 4, 3, 6), (1, 1, 1, -1)
+    U = synth.random_links(dims, 0.4, 5001).astype(np.complex64)
+    c = synth.random_coeffs(5002)
+    psi = synth.gaussian_source(dims, 5003)
+    W = ok.precompute_W(to_dev(U), c, bc, ok.W_F64)
+    got = ok.apply_M(W, to_dev(psi)).cpu().numpy()
+    exp = wform.apply(U.astype(np.complex128), c, psi, bc)
+    assert rel_l2(got, exp) < FP64_TOL
+
+
+def test_apply_is_linear_and_deterministic():
+    dims = (6, 5, 4, 7)
+    U = synth.random_links(dims, 0.4, 6001)
+    W = ok.precompute_W(to_dev(U), synth.random_coeffs(6002), (1, 1, 1, -1), ok.W_F64 | ok.W_F32)
+    a = to_dev(synth.gaussian_source(dims, 6003))
+    b = to_dev(synth.gaussian_source(dims, 6004))
+    Ma, Mb = ok.apply_M(W, a), ok.apply_M(W, b)
+    Mab = ok.apply_M(W, a * (0.3 - 1.1j) + b)
+    assert torch.allclose(Mab, Ma * (0.3 - 1.1j) + Mb, rtol=0, atol=1e-12 * float(Mab.abs().max()))
+    assert torch.equal(ok.apply_M(W, a), Ma)
+    a32 = a.to(torch.complex64)
+    assert torch.equal(ok.apply_M(W, a32), ok.apply_M(W, a32))
+
+
+def _sample_sites(V, n=64, seed=0):
+    rng = np.random.default_rng(seed)
+    fixed = [0, 1, 31, 32, 127, 128, V // 2, V - 129, V - 33, V - 1]
+    return np.unique(np.concatenate([fixed, rng.integers(0, V, n - len(fixed))]))
+
+
+def test_full_size_16cube32_sampled():
+    """The 16^3 x 32 workload in the launch configuration the benchmark uses: FP64 and FP32 applies
+    against the oracle evaluated site by site at 64 sampled sites."""
+    name = "16^3x32"
+    dims, U, c, src = synth.workload_inputs(name)
+    W = ok.precompute_W(to_dev(U), c, (1, 1, 1, 1), ok.W_F64 | ok.W_F32)
+    V = int(np.prod(dims))
+    sites = _sample_sites(V)
+    exp = direct.apply_at(U, c, src, sites)
+    got64 = ok.apply_M(W, to_dev(src)).cpu().numpy().reshape(V, 4, 3)[sites]
+    got32 = ok.apply_M(W, to_dev(src.astype(np.complex64))).cpu().numpy().reshape(V, 4, 3)[sites]
+    assert rel_max(got64, exp) < 10 * FP64_TOL
+    assert rel_l2(got32, exp) < FP32_TOL
+    assert abs(W.u0 - gauge.tadpole_u0(U)) < 1e-13
+    # the handle holds 43 colour matrices per site in each precision
+    assert W.nbytes == ((V + 31) // 32) * 32 * 43 * 9 * (16 + 8)
+
+
+@pytest.mark.slow
+def test_max_size_28cube96_sampled():
+    """The largest workload (28^3 x 96, 2.1M sites): FP64 and FP32 W (19.6 GB) fit and the FP32
+    apply matches the oracle at sampled sites."""
+    name = "28^3x96"
+    dims, U, c, src = synth.workload_inputs(name)
+    V = int(np.prod(dims))
+    W = ok.precompute_W(to_dev(U), c, (1, 1, 1, 1), ok.W_F64 | ok.W_F32)
+    sites = _sample_sites(V, 48, seed=1)
+    exp = direct.apply_at(U, c, src, sites)
+    psi = to_dev(src)
+    got64 = ok.apply_M(W, psi).cpu().numpy().reshape(V, 4, 3)[sites]
+    assert rel_max(got64, exp) < 10 * FP64_TOL
+    del psi
+    got32 = ok.apply_M(W, to_dev(src.astype(np.complex64))).cpu().numpy().reshape(V, 4, 3)[sites]
+    assert rel_l2(got32, exp) < FP32_TOL
+
+
+def test_native_kernels_run():
+    """The CUDA library is what runs: its own launch counter moves with every apply."""
+    dims = (4, 4, 4, 4)
+    W = ok.precompute_W(to_dev(synth.random_links(dims, 0.3, 7001)), synth.placeholder_coeffs(1.0))
+    n0 = ok.launch_count()
+    ok.apply_M(W, to_dev(synth.gaussian_source(dims, 7002)))
+    torch.cuda.synchronize()
+    assert ok.launch_count() == n0 + 1
+
+
+def test_argument_errors():
+    dims = (4, 4, 4, 4)
+    U = to_dev(synth.random_links(dims, 0.3, 8001))
+    W32 = ok.precompute_W(U, synth.placeholder_coeffs(1.0), precisions=ok.W_F32)
+    psi64 = to_dev(synth.gaussian_source(dims, 8002))
+    with pytest.raises(ok.OKError):          # handle has no FP64 copy
+        ok.apply_M(W32, psi64)
+    with pytest.raises(ok.OKError):          # FP64 solve needs the FP64 copy
+        ok.bicgstab(W32, psi64)
+    psi32 = psi64.to(torch.complex64)
+    with pytest.raises(ok.OKError):          # out aliases psi
+        ok.apply_M(W32, psi32, out=psi32)
+    with pytest.raises(ok.OKError):          # bad kind
+        ok.W_expand(W32, 14, ok.F32)
+    with pytest.raises(ok.OKError):          # bad boundary phase
+        ok.precompute_W(U, synth.placeholder_coeffs(1.0), bc=(1, 1, 1, 2))
+    with pytest.raises(ok.OKError):          # non-finite coefficient
+        ok.precompute_W(U, synth.placeholder_coeffs(1.0).replace(c3=float("nan")))
+    with pytest.raises(ValueError):
+        ok.apply_M(W32, psi32[:10])
