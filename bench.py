@@ -1,0 +1,400 @@
+#!/usr/bin/env python3
+"""Benchmark of the OK-action W-form hot path on one GB300 (or N independent replicas).
+
+A step is one pass of the whole path over the 16^3 x 32 workload (random SU(3) links, eps 0.2,
+am0 0.5, Gaussian source), with inputs resident in HBM:
+  precompute W from the links (mean plaquette / u0, clover, W matrices; FP64 and FP32 copies),
+  BiCGStab solve of M x = b to a true FP64 residual |b - M x| / |b| < 1e-10 (FP32 iteration with
+  FP64 reliable updates), release of W.
+`value` is the step's algorithmic HBM traffic (bytes each kernel must move once) divided by the
+step time, in GB/s.  `roofline` describes the dominant kernel (the FP32 application of M inside
+the solve) timed with CUDA events on its own stream during the timed steps.  `e2e` repeats the
+step through the public API with the links and the source copied from pinned host memory and the
+solution copied back inside the timed region.
+
+--impl reference times the oracle (plain FP64 numpy CPU code) on the same workload and metric: each
+step is one oracle application of M on the full lattice (a bounded sample of the solve).
+
+Multi-GPU: one process per GPU under torch.distributed; each rank solves its own replica (its own
+source), so the work per GPU is fixed ("scaling": "weak") and no data moves between ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("M·ψ HBM GB/s (% peak); time to 1e-10 solve, chosen form vs plain FP64 BiCGStab")
+WORKLOAD = "16^3x32"
+TOL = 1e-10
+
+# Algorithmic bytes per site (each stored byte read once, each output written once).
+W64_BYTES = 43 * 9 * 16          # stored FP64 W per site
+W32_BYTES = 43 * 9 * 8           # stored FP32 W per site
+SPINOR64, SPINOR32 = 192, 96
+LINKS64 = 4 * 9 * 16
+APPLY64 = W64_BYTES + 2 * SPINOR64            # 6576: W + psi in + out
+APPLY32 = W32_BYTES + 2 * SPINOR32            # 3288
+RESID64 = APPLY64 + SPINOR64                  # true residual also reads b
+PRECOMPUTE = LINKS64 + W64_BYTES + W32_BYTES  # links in, both W copies out
+# FP32 vector traffic per BiCGStab iteration: <rhat, v> reads rhat (1); s = r - a v (3);
+# x += a p + w s, r = s - w t with two dots (5 reads + 2 writes); p = r + b (p - w v) (4).
+ITER_VEC32 = (1 + 3 + 7 + 4) * SPINOR32
+ITER_VEC64 = (1 + 3 + 7 + 4) * SPINOR64
+# Mixed-precision reliable update: x64 += x32 and x32 = 0 (2 + 2 vectors, one of each width),
+# demotion r64 -> r32 with <rhat, r> (3), update of p (4 FP32 vectors).
+RELIABLE32 = 2 * SPINOR64 + 2 * SPINOR32 + (SPINOR64 + 2 * SPINOR32) + 4 * SPINOR32
+RESTART64 = 3 * SPINOR64
+
+
+def solve_bytes(V, info, mode):
+    """Algorithmic bytes of one solve from its counters."""
+    it = info["iters"]
+    if mode == "mixed":
+        per_iter = 2 * APPLY32 + ITER_VEC32
+        extra = info["fp64_applies"] * RESID64 + (info["reliable_updates"] + info["restarts"] + 1) * RELIABLE32
+    else:
+        per_iter = 2 * APPLY64 + ITER_VEC64
+        extra = info["fp64_applies"] * RESID64 + (info["restarts"] + 1) * RESTART64
+    return V * (it * per_iter + extra)
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["mixed", "f64"], default="mixed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solve")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return rank, world
+
+
+def reduce_max_sum(times_ms, units, device=None):
+    """(max over ranks of times_ms, sum over ranks of units); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(times_ms), float(units)
+    t = torch.tensor([float(times_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock and throttle samples (every 200 ms) while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if _isnum(r[3]))
+                if any(_isnum(r[3]) for r in rows) else None}
+
+
+def _isnum(s):
+    try:
+        float(s)
+        return True
+    except ValueError:
+        return False
+
+
+# ----------------------------------------------------------------------------- roofline inputs
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def apply_source_hash():
+    h = hashlib.sha256()
+    for f in ("ok_apply.cu", "ok_internal.cuh", "ok_reduce.cuh", "ok_launch.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1311_5029_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """DRAM bytes per launch recorded by the committed ncu summary, if it still matches the source."""
+    path = os.path.join(ROOT, "profiles", "apply_f32_16x16x16x32.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_src = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    m_b = re.search(rf"{kernel_key}_dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_src or not m_b or m_src.group(1) != apply_source_hash():
+        return None
+    return float(m_b.group(1))
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_sample(dims, U, c, b):
+    """One oracle application of M on the full lattice: (seconds, threads used, bytes counted)."""
+    from oracle import wform
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    c0 = time.process_time()
+    t0 = time.perf_counter()
+    wform.apply_lean(U, c, b, (1, 1, 1, 1))
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    cores = max(1, round(cpu / wall)) if wall > 0 else 1
+    return wall, cores, APPLY64 * V
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import synth
+    import paper_1311_5029_gb300 as ok
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init("nccl")
+    dev = torch.device("cuda", local)
+    ok.load()
+    dims, U, c, b = synth.workload_inputs(WORKLOAD, source_seed=7 + rank)
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    bc = (1, 1, 1, 1)
+    U_d = torch.from_numpy(U).to(dev)
+    b_d = torch.from_numpy(b).to(dev)
+    precs = ok.W_F64 | (ok.W_F32 if args.mode == "mixed" else 0)
+    mode = ok.SOLVE_MIXED if args.mode == "mixed" else ok.SOLVE_F64
+
+    def step(links, src):
+        W = ok.precompute_W(links, c, bc, precs)
+        x = torch.zeros_like(src)
+        x, info = ok.bicgstab(W, src, x, tol=TOL, mode=mode)
+        W.free()
+        return x, info
+
+    # plain FP64 BiCGStab on the same system: the comparison the metric names (untimed here;
+    # its own time to solution comes from CUDA events around the call)
+    plain = None
+    if not args.no_plain and args.mode == "mixed":
+        W = ok.precompute_W(U_d, c, bc, ok.W_F64)
+        ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev_a.record()
+        _, pinfo = ok.bicgstab(W, b_d, tol=TOL, mode=ok.SOLVE_F64)
+        ev_b.record()
+        torch.cuda.synchronize()
+        plain = {"solve_ms": ev_a.elapsed_time(ev_b), "iters": pinfo["iters"], "true_relres": pinfo["true_relres"]}
+        W.free()
+
+    for _ in range(args.warmup):
+        step(U_d, b_d)
+    torch.cuda.synchronize()
+
+    ok.trace_reset()
+    ok.trace_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    n0 = ok.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    tot_bytes, infos = 0, []
+    for _ in range(args.steps):
+        _, info = step(U_d, b_d)
+        infos.append(info)
+        tot_bytes += V * PRECOMPUTE + solve_bytes(V, info, args.mode)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = ok.launch_count() - n0
+    clk = clocks.stop()
+    ok.trace_enable(False)
+    trace = ok.trace_read()
+    local_ms = e0.elapsed_time(e1)
+    ms_all, bytes_all = reduce_max_sum(local_ms, tot_bytes, dev)
+    value = bytes_all / (ms_all * 1e-3) / 1e9
+    ms_per_step = ms_all / args.steps
+
+    # dominant kernel: the FP32 (or FP64) application of M inside the solve
+    key = "apply_f32" if args.mode == "mixed" else "apply_f64"
+    per_launch = APPLY32 if args.mode == "mixed" else APPLY64
+    n_apply = sum(v[0] for k, v in trace.items() if k in (key + "_dot", key + "_ts"))
+    ms_apply = sum(v[1] for k, v in trace.items() if k in (key + "_dot", key + "_ts"))
+    peak, peak_kind = measured_peaks()
+    achieved = per_launch * V / (ms_apply / n_apply * 1e-3) / 1e9 if n_apply else None
+    traffic = ncu_traffic(key)
+    roof = {"kernel": key, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_source": peak_kind,
+            "unit": "GB/s", "frac": achieved / peak if achieved else None, "traffic": traffic,
+            "algorithmic_bytes_per_launch": per_launch * V, "launches": n_apply,
+            "avg_launch_us": ms_apply / n_apply * 1e3 if n_apply else None}
+    step_ms = sum(v[1] for v in trace.values())
+    shares = {k: round(v[1] / step_ms, 4) for k, v in sorted(trace.items(), key=lambda kv: -kv[1][1])} if step_ms else {}
+
+    # end to end through the public API, host buffers in and out
+    e2e = None
+    if not args.no_e2e:
+        U_h = torch.from_numpy(U).pin_memory()
+        b_h = torch.from_numpy(b).pin_memory()
+        x_h = torch.empty_like(b_h).pin_memory()
+        U_e = torch.empty_like(U_d)
+        b_e = torch.empty_like(b_d)
+        barrier()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        e2e_bytes = 0
+        for _ in range(args.steps):
+            U_e.copy_(U_h, non_blocking=True)
+            b_e.copy_(b_h, non_blocking=True)
+            x, info = step(U_e, b_e)
+            x_h.copy_(x, non_blocking=True)
+            e2e_bytes += V * PRECOMPUTE + solve_bytes(V, info, args.mode)
+        f1.record()
+        torch.cuda.synchronize()
+        barrier()
+        e_ms, e_bytes = reduce_max_sum(f0.elapsed_time(f1), e2e_bytes, dev)
+        e2e = {"value": e_bytes / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e_ms / args.steps,
+               "h2d_bytes_per_step": U_h.numel() * U_h.element_size() + b_h.numel() * b_h.element_size(),
+               "d2h_bytes_per_step": x_h.numel() * x_h.element_size()}
+
+    if rank != 0:
+        return None
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        wall, cores, nbytes = oracle_sample(dims, U, c, b)
+        cpu = {"value": nbytes / wall / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "sample": f"one oracle application of M (W formulas re-evaluated inside, FP64 numpy) on the full "
+                         f"{WORKLOAD} lattice, {wall:.1f} s, counted as one FP64 apply ({APPLY64} B/site)"}
+    iters = [i["iters"] for i in infos]
+    solve_ms = statistics.median(i["time_ms"] for i in infos)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice_xyzt": list(dims), "sites": V, "links_eps": 0.2, "am0": 0.5,
+                   "source": "gaussian", "tol": TOL,
+                   "solver": "BiCGStab FP32 + FP64 reliable updates" if args.mode == "mixed" else "BiCGStab FP64",
+                   "step": "precompute W (FP64+FP32) + solve to 1e-10 true residual + free W",
+                   "l2": "inputs larger than L2 (W = %.2f GB per step)" % (V * (W64_BYTES + W32_BYTES) / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "percent_of_hbm_peak": 100.0 * value / peak,
+        "kernel_time_shares": shares,
+        "solve": {"iters_median": statistics.median(iters), "solve_ms_median": solve_ms,
+                  "reliable_updates": infos[-1]["reliable_updates"], "true_relres": infos[-1]["true_relres"]},
+        "plain_fp64": plain,
+        "time_to_solution_ratio_plain_over_chosen": (plain["solve_ms"] / solve_ms) if plain else None,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+    }
+    return line
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    import synth
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    dims, U, c, b = synth.workload_inputs(WORKLOAD)
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    for _ in range(args.warmup):
+        oracle_sample(dims, U, c, b)
+    walls, cores = [], 1
+    for _ in range(args.steps):
+        w, cores, nbytes = oracle_sample(dims, U, c, b)
+        walls.append(w)
+    total = sum(walls)
+    value = args.steps * APPLY64 * V / total / 1e9
+    sample = (f"each step one oracle application of M (FP64 numpy, W formulas re-evaluated inside) on the full "
+              f"{WORKLOAD} lattice, counted as one FP64 apply ({APPLY64} B/site)")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice_xyzt": list(dims), "sites": V},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    try:
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized():
+            dist.destroy_process_group()
+    except Exception:
+        pass
+
+
+if __name__ == "__main__":
+    main()

@@ -152,6 +152,22 @@ int ok_W_expand(const ok_W* W, ok_prec prec, int kind, void* out, void* stream);
 /* Number of kernels this library has launched since it was loaded (all devices, all threads). */
 unsigned long long ok_launch_count(void);
 
+/* Kernel tracing (per-kernel-class timing with CUDA events recorded on the launching stream).
+ * While enabled, every kernel launch of the library is bracketed by two CUDA events; ok_trace_read
+ * waits for the recorded events, folds them into per-class totals and returns up to `max` entries
+ * in `stats` (host array), the number of classes in *n.  Classes are named after the kernel and
+ * its precision, e.g. "apply_f32_dot".  ok_trace_reset clears the totals.  Returns OK_EINVAL for
+ * null outputs, OK_ECUDA if an event failed.  Tracing adds two event records per launch. */
+typedef struct {
+    char name[32];
+    unsigned long long launches;
+    double total_ms;
+} ok_trace_stat;
+
+void ok_trace_enable(int on);
+int ok_trace_read(ok_trace_stat* stats, int max, int* n);
+void ok_trace_reset(void);
+
 /* Last CUDA error code seen by the library on this thread (0 if none). */
 int ok_last_cuda_error(void);
 

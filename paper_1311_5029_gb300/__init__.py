@@ -22,7 +22,7 @@ from .build import LIB, build as build_library
 __all__ = [
     "load", "precompute_W", "apply_M", "bicgstab", "true_residual", "W_expand", "launch_count",
     "strerror", "OKError", "WHandle", "F64", "F32", "W_F64", "W_F32", "SOLVE_AUTO", "SOLVE_F64",
-    "SOLVE_MIXED", "header_functions",
+    "SOLVE_MIXED", "header_functions", "trace_enable", "trace_read", "trace_reset",
 ]
 
 F64, F32 = 0, 1
@@ -51,6 +51,10 @@ class ok_solve_info(ctypes.Structure):
 class ok_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("mode", ctypes.c_int),
                 ("delta", ctypes.c_double), ("max_restarts", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class ok_trace_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_ulonglong), ("total_ms", ctypes.c_double)]
 
 
 class OKError(RuntimeError):
@@ -86,6 +90,9 @@ def load(path: str | None = None):
         "ok_true_residual": (i, [vp, vp, vp, ctypes.POINTER(d), vp]),
         "ok_W_expand": (i, [vp, i, i, vp, vp]),
         "ok_launch_count": (ctypes.c_ulonglong, []),
+        "ok_trace_enable": (None, [i]),
+        "ok_trace_read": (i, [ctypes.POINTER(ok_trace_stat), i, ctypes.POINTER(i)]),
+        "ok_trace_reset": (None, []),
         "ok_last_cuda_error": (i, []),
         "ok_strerror": (ctypes.c_char_p, [i]),
     }
@@ -111,6 +118,24 @@ def strerror(status: int) -> str:
 def launch_count() -> int:
     """Kernels launched by the library since it was loaded."""
     return int(load().ok_launch_count())
+
+
+def trace_enable(on: bool = True):
+    """Bracket every kernel launch of the library with CUDA events (per-class timing)."""
+    load().ok_trace_enable(1 if on else 0)
+
+
+def trace_reset():
+    load().ok_trace_reset()
+
+
+def trace_read() -> dict:
+    """{kernel class: (launches, total_ms)} accumulated since the last reset (waits for the events)."""
+    lib = load()
+    n = ctypes.c_int(0)
+    buf = (ok_trace_stat * 64)()
+    _check(lib.ok_trace_read(buf, 64, ctypes.byref(n)), "ok_trace_read")
+    return {buf[k].name.decode(): (int(buf[k].launches), float(buf[k].total_ms)) for k in range(min(n.value, 64))}
 
 
 def _check(status: int, where: str):

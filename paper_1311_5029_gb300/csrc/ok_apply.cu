@@ -454,12 +454,17 @@ int launch_apply(const ok_W* Wh, const cx<R>* psi, cx<R>* out, int epi, const Ep
   const Geom& g = Wh->g;
   int nb = grid_for(g.V, APPLY_THREADS);
   R c0q = (R)Wh->sc.c0q, a = (R)Wh->sc.a_ii, b = (R)Wh->sc.b_ii;
-  switch (epi) {
-    case EPI_NONE: apply_kernel<R, EPI_NONE><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-    case EPI_DOT: apply_kernel<R, EPI_DOT><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-    case EPI_TS: apply_kernel<R, EPI_TS><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-    case EPI_RESID: apply_kernel<R, EPI_RESID><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-    default: return OK_EINVAL;
+  static const char* names64[4] = {"apply_f64", "apply_f64_dot", "apply_f64_ts", "apply_f64_resid"};
+  static const char* names32[4] = {"apply_f32", "apply_f32_dot", "apply_f32_ts", "apply_f32_resid"};
+  if (epi < EPI_NONE || epi > EPI_RESID) return OK_EINVAL;
+  {
+    TraceScope ts(sizeof(R) == 8 ? names64[epi] : names32[epi], st);
+    switch (epi) {
+      case EPI_NONE: apply_kernel<R, EPI_NONE><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+      case EPI_DOT: apply_kernel<R, EPI_DOT><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+      case EPI_TS: apply_kernel<R, EPI_TS><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+      default: apply_kernel<R, EPI_RESID><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+    }
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;

@@ -187,7 +187,10 @@ template <typename R>
 int launch_update_s(const cx<R>* r, const cx<R>* v, cx<R>* s, long long n, const SolverState* st, cudaStream_t strm) {
   using T = typename Unit<R>::T;
   long long nu = units_of<R>(n);
-  update_s_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((const T*)r, (const T*)v, (T*)s, nu, st);
+  {
+    TraceScope ts(sizeof(R) == 8 ? "update_s_f64" : "update_s_f32", strm);
+    update_s_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((const T*)r, (const T*)v, (T*)s, nu, st);
+  }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
 }
@@ -198,8 +201,11 @@ int launch_update_xr(cx<R>* x, const cx<R>* p, const cx<R>* s, const cx<R>* t, c
   using T = typename Unit<R>::T;
   long long nu = units_of<R>(n);
   RedArgs ra{st, part, nullptr, FIN_XR};
-  update_xr_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r,
+  {
+    TraceScope ts(sizeof(R) == 8 ? "update_xr_f64" : "update_xr_f32", strm);
+    update_xr_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r,
                                                                   (const T*)rhat, nu, st, ra);
+  }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
 }
@@ -208,7 +214,10 @@ template <typename R>
 int launch_update_p(cx<R>* p, const cx<R>* r, const cx<R>* v, long long n, const SolverState* st, cudaStream_t strm) {
   using T = typename Unit<R>::T;
   long long nu = units_of<R>(n);
-  update_p_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((T*)p, (const T*)r, (const T*)v, nu, st);
+  {
+    TraceScope ts(sizeof(R) == 8 ? "update_p_f64" : "update_p_f32", strm);
+    update_p_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((T*)p, (const T*)r, (const T*)v, nu, st);
+  }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
 }
@@ -218,7 +227,10 @@ int launch_restart(const cx<R>* r, cx<R>* rhat, cx<R>* p, long long n, SolverSta
   using T = typename Unit<R>::T;
   long long nu = units_of<R>(n);
   RedArgs ra{st, part, nullptr, FIN_RESTART};
-  restart_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((const T*)r, (T*)rhat, (T*)p, nu, st, ra);
+  {
+    TraceScope ts(sizeof(R) == 8 ? "restart_f64" : "restart_f32", strm);
+    restart_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((const T*)r, (T*)rhat, (T*)p, nu, st, ra);
+  }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
 }
@@ -228,17 +240,26 @@ int launch_demote(const cx<double>* r64, cx<float>* r32, cx<float>* rhat, cx<flo
   int nb = blas_blocks(n);
   if (restart) {
     RedArgs ra{st, part, nullptr, FIN_RESTART};
+    {
+    TraceScope ts("demote_restart", strm);
     demote_kernel<true><<<nb, BLAS_THREADS, 0, strm>>>((const double2*)r64, (float2*)r32, (float2*)rhat, (float2*)p, n, st, ra);
+  }
   } else {
     RedArgs ra{st, part, nullptr, FIN_CONTINUE};
+    {
+    TraceScope ts("demote_continue", strm);
     demote_kernel<false><<<nb, BLAS_THREADS, 0, strm>>>((const double2*)r64, (float2*)r32, (float2*)rhat, (float2*)p, n, st, ra);
+  }
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
 }
 
 int launch_accum_x(cx<double>* x64, cx<float>* x32, long long n, cudaStream_t strm) {
-  accum_x_kernel<<<blas_blocks(n), BLAS_THREADS, 0, strm>>>((double2*)x64, (float2*)x32, n);
+  {
+    TraceScope ts("accum_x", strm);
+    accum_x_kernel<<<blas_blocks(n), BLAS_THREADS, 0, strm>>>((double2*)x64, (float2*)x32, n);
+  }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
 }

@@ -3,6 +3,11 @@
 
 #include <atomic>
 #include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
 
 namespace okgb {
 
@@ -10,6 +15,50 @@ static std::atomic<unsigned long long> g_launches{0};
 static thread_local int g_last_cuda_error = 0;
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------- tracing
+namespace {
+struct TraceRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+struct TraceTotals {
+  unsigned long long launches = 0;
+  double ms = 0.0;
+};
+std::atomic<int> g_trace_on{0};
+std::mutex g_trace_mu;
+std::vector<TraceRec> g_pending;
+std::vector<cudaEvent_t> g_event_pool;
+std::map<std::string, TraceTotals> g_totals;
+
+cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+}  // namespace
+
+TraceScope::TraceScope(const char* n, cudaStream_t s) : name(n), st(s), slot(-1) {
+  if (!g_trace_on.load(std::memory_order_relaxed)) return;
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  TraceRec r{n, take_event(), take_event()};
+  if (!r.a || !r.b) return;
+  if (cudaEventRecord(r.a, s) != cudaSuccess) return;
+  g_pending.push_back(r);
+  slot = (int)g_pending.size() - 1;
+}
+
+TraceScope::~TraceScope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  if (slot < (int)g_pending.size()) cudaEventRecord(g_pending[slot].b, st);
+}
 unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
 void set_cuda_error(cudaError_t e) { g_last_cuda_error = (int)e; }
 
@@ -102,6 +151,49 @@ int ok_W_expand(const ok_W* W, ok_prec prec, int kind, void* out, void* stream) 
 }
 
 unsigned long long ok_launch_count(void) { return launches(); }
+
+void ok_trace_enable(int on) { g_trace_on.store(on ? 1 : 0); }
+
+int ok_trace_read(ok_trace_stat* stats, int max, int* n) {
+  if (!stats || !n || max < 0) return OK_EINVAL;
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  int rc = OK_SUCCESS;
+  for (TraceRec& r : g_pending) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) { set_cuda_error(e); rc = OK_ECUDA; continue; }
+    TraceTotals& t = g_totals[r.name];
+    t.launches += 1;
+    t.ms += ms;
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_pending.clear();
+  int k = 0;
+  for (auto& kv : g_totals) {
+    if (k < max) {
+      std::memset(stats[k].name, 0, sizeof(stats[k].name));
+      std::strncpy(stats[k].name, kv.first.c_str(), sizeof(stats[k].name) - 1);
+      stats[k].launches = kv.second.launches;
+      stats[k].total_ms = kv.second.ms;
+    }
+    ++k;
+  }
+  *n = k;
+  return rc;
+}
+
+void ok_trace_reset(void) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  for (TraceRec& r : g_pending) {
+    cudaEventSynchronize(r.b);
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_pending.clear();
+  g_totals.clear();
+}
 
 int ok_last_cuda_error(void) { return g_last_cuda_error; }
 

@@ -103,6 +103,15 @@ void count_launch();
 unsigned long long launches();
 void set_cuda_error(cudaError_t e);
 
+// Brackets one kernel launch with CUDA events when tracing is enabled (ok_trace_enable).
+struct TraceScope {
+  const char* name;
+  cudaStream_t st;
+  int slot;
+  TraceScope(const char* n, cudaStream_t s);
+  ~TraceScope();
+};
+
 inline int grid_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
 
 }  // namespace okgb

@@ -481,14 +481,23 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
   const Geom& g = W->g;
   const cx<LT>* U = (const cx<LT>*)links;
   int nb1 = grid_for(g.V, K1_THREADS);
-  clover_kernel<LT><<<nb1, K1_THREADS, 0, st>>>(U, g, EB, part);
+  {
+    TraceScope ts("clover", st);
+    clover_kernel<LT><<<nb1, K1_THREADS, 0, st>>>(U, g, EB, part);
+  }
   OK_LAUNCH_CHECK();
-  scalars_kernel<<<1, 256, 0, st>>>(part, nb1, g, *c, dsc);
+  {
+    TraceScope ts("plaquette_u0", st);
+    scalars_kernel<<<1, 256, 0, st>>>(part, nb1, g, *c, dsc);
+  }
   OK_LAUNCH_CHECK();
   WOut o{(cx<double>*)W->W64, (cx<float>*)W->W32};
   int nb2 = grid_for(g.V, K2_THREADS);
   for (int part_id = 0; part_id < 5; ++part_id) {
+    {
+    TraceScope ts("w_build", st);
     w_kernel<LT><<<nb2, K2_THREADS, 0, st>>>(U, EB, g, *c, dsc, o, part_id);
+  }
     OK_LAUNCH_CHECK();
   }
   return OK_SUCCESS;
@@ -568,6 +577,7 @@ int expand(const ok_W* W, ok_prec prec, int kind, void* out, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(dsc, &W->sc, sizeof(WScalars), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) { cudaFreeAsync(dsc, st); set_cuda_error(e); return OK_ECUDA; }
   int nb = grid_for(W->g.V, 64);
+  TraceScope ts("expand", st);
   if (prec == OK_F64)
     expand_kernel<double><<<nb, 64, 0, st>>>((const cx<double>*)src, W->g, dsc, kind, (cx<double>*)out);
   else

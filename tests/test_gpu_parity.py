@@ -171,4 +171,4 @@ def test_argument_errors():
     with pytest.raises(ok.OKError):          # non-finite coefficient
         ok.precompute_W(U, synth.placeholder_coeffs(1.0).replace(c3=float("nan")))
     with pytest.raises(ValueError):
-        ok.apply_M(W32, psi32[:10])
+        ok.apply_M(W32, psi32.reshape(-1)[:10])
