@@ -125,7 +125,7 @@ int ok_W_info(const ok_W* W, ok_lattice* lat, int* W_precs, size_t* bytes);
 int ok_apply_M(const ok_W* W, ok_prec prec, const void* psi, void* out, void* stream);
 
 /* Solve M x = src by BiCGStab (the paper's bi-stabilized CG, Sec. 2.3) with default parameters
- * (OK_SOLVE_AUTO, delta 0.1, 5 restarts).  src, x: device [V][4][3] complex128; x holds the
+ * (OK_SOLVE_AUTO, delta 1e-3, 5 restarts, host check every 4 iterations).  src, x: device [V][4][3] complex128; x holds the
  * initial guess on entry and the solution on exit.  info (host, may be NULL) is filled on
  * success and on OK_ENOCONV / OK_EBREAKDOWN.  Synchronises `stream`. */
 int ok_bicgstab(const ok_W* W, const void* src, void* x, double tol, int maxiter,

@@ -246,8 +246,8 @@ def apply_M(W: WHandle, psi, out=None, stream=None):
     return out
 
 
-def bicgstab(W: WHandle, src, x=None, tol=1e-10, maxiter=20000, mode=SOLVE_AUTO, delta=0.1, max_restarts=5,
-             check_every=8, stream=None, raise_on_noconv=True):
+def bicgstab(W: WHandle, src, x=None, tol=1e-10, maxiter=20000, mode=SOLVE_AUTO, delta=1e-3, max_restarts=5,
+             check_every=4, stream=None, raise_on_noconv=True):
     """ok_bicgstab_ex: solve M x = src (complex128).  Returns (x, info dict)."""
     import torch
     _field_check(W, src, "src")

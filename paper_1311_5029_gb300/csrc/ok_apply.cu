@@ -446,12 +446,407 @@ __global__ void __launch_bounds__(APPLY_THREADS) apply_kernel(const cx<R>* __res
   }
 }
 
+// ============================================================================ two threads per site
+// The pair (lanes 2k, 2k+1) shares one site.  Thread p = 0 accumulates acc+ and loads the upper
+// spin half u of every spinor it needs, thread p = 1 accumulates acc- and loads the lower half l;
+// the other half arrives through one shuffle.  Spatial hops then split without duplicated work:
+// p = 0 uses (D + S)/2 forward and (D - S)/2 backward, p = 1 the other two.  W^0, the temporal hop
+// and the colour matrices of the two-hop terms are read by both threads (the same addresses, one
+// transaction per warp).  Half the registers per thread and twice the warps per SM keep more
+// global loads in flight than one thread per site can.
+
+template <typename R> struct H6 { cx<R> v[2][3]; };
+
+template <typename R>
+__device__ __forceinline__ void load_half(const cx<R>* __restrict__ psi, int site, int p, H6<R>& h) {
+  if constexpr (sizeof(R) == 8) {
+    const double2* q = reinterpret_cast<const double2*>(psi) + (size_t)site * 12 + 6 * p;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      double2 d = __ldg(q + k);
+      h.v[k / 3][k % 3] = mk<R>(d.x, d.y);
+    }
+  } else {
+    const float4* q = reinterpret_cast<const float4*>(psi) + (size_t)site * 6 + 3 * p;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float4 d = __ldg(q + k);
+      h.v[(2 * k) / 3][(2 * k) % 3] = mk<R>(d.x, d.y);
+      h.v[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk<R>(d.z, d.w);
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void store_half(cx<R>* __restrict__ out, int site, int p, const H6<R>& h) {
+  if constexpr (sizeof(R) == 8) {
+    double2* q = reinterpret_cast<double2*>(out) + (size_t)site * 12 + 6 * p;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q[k] = make_double2(h.v[k / 3][k % 3].re, h.v[k / 3][k % 3].im);
+  } else {
+    float4* q = reinterpret_cast<float4*>(out) + (size_t)site * 6 + 3 * p;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const cx<R>& a = h.v[(2 * k) / 3][(2 * k) % 3];
+      const cx<R>& b = h.v[(2 * k + 1) / 3][(2 * k + 1) % 3];
+      q[k] = make_float4(a.re, a.im, b.re, b.im);
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ H6<R> partner(const H6<R>& h, unsigned mask) {
+  H6<R> o;
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      o.v[s][a].re = __shfl_xor_sync(mask, h.v[s][a].re, 1);
+      o.v[s][a].im = __shfl_xor_sync(mask, h.v[s][a].im, 1);
+    }
+  return o;
+}
+
+struct Pair {
+  int p;          // 0: acc+ thread, 1: acc- thread
+  unsigned mask;  // the two lanes of the pair
+};
+
+// Gather the neighbour at offset D: mine = own half, oth = partner's half, h = h+ (p = 0) or h- (p = 1).
+template <typename R, int D0, int D1, int D2, int D3>
+__device__ __forceinline__ int gather_pair(const cx<R>* __restrict__ psi, const int (&c)[4], const Geom& g, const Pair& pr,
+                                           H6<R>& h, H6<R>* u = nullptr, H6<R>* l = nullptr) {
+  bool neg;
+  int n = nbr_site<D0, D1, D2, D3>(c, g, neg);
+  H6<R> mine;
+  load_half<R>(psi, n, pr.p, mine);
+  if (neg) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) mine.v[s][a] = -mine.v[s][a];
+  }
+  H6<R> oth = partner(mine, pr.mask);
+  // p = 0: h+ = mine + oth (u = mine);  p = 1: h- = oth - mine (u = oth)
+  const R sg = pr.p ? R(-1) : R(1);
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cx<R> m = mine.v[s][a], o = oth.v[s][a];
+      h.v[s][a] = mk<R>(sg * m.re + o.re, sg * m.im + o.im);
+      if (u) u->v[s][a] = pr.p ? o : m;
+      if (l) l->v[s][a] = pr.p ? m : o;
+    }
+  return n;
+}
+
+template <typename R, bool DAG>
+__device__ __forceinline__ void block2h(const cx<R>* __restrict__ W, int site, int m, const H6<R>& h, H6<R>& acc) {
+  M3<R> b;
+  b = wmat(W, site, m + 0);
+  if (DAG) mdv_add(acc.v[0], b, h.v[0]); else mv_add(acc.v[0], b, h.v[0]);
+  b = wmat(W, site, m + 1);
+  if (DAG) mdv_add(acc.v[1], b, h.v[0]); else mv_add(acc.v[0], b, h.v[1]);
+  b = wmat(W, site, m + 2);
+  if (DAG) mdv_add(acc.v[0], b, h.v[1]); else mv_add(acc.v[1], b, h.v[0]);
+  b = wmat(W, site, m + 3);
+  if (DAG) mdv_add(acc.v[1], b, h.v[1]); else mv_add(acc.v[1], b, h.v[1]);
+}
+
+template <typename R>
+__device__ __forceinline__ void add_sigma_h(H6<R>& acc, int k, const H6<R>& y, R f) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (k == 0) {
+      acc.v[0][a] = acc.v[0][a] + f * y.v[1][a];
+      acc.v[1][a] = acc.v[1][a] + f * y.v[0][a];
+    } else if (k == 1) {
+      acc.v[0][a] = acc.v[0][a] + f * tmi(y.v[1][a]);
+      acc.v[1][a] = acc.v[1][a] + f * ti(y.v[0][a]);
+    } else {
+      acc.v[0][a] = acc.v[0][a] + f * y.v[0][a];
+      acc.v[1][a] = acc.v[1][a] - f * y.v[1][a];
+    }
+  }
+}
+
+template <typename R, bool DAG>
+__device__ __forceinline__ void colour2h(H6<R>& y, const M3<R>& V, const H6<R>& h) {
+  if (DAG) { mdv(y.v[0], V, h.v[0]); mdv(y.v[1], V, h.v[1]); }
+  else { mv(y.v[0], V, h.v[0]); mv(y.v[1], V, h.v[1]); }
+}
+
+template <typename R, int I>
+__device__ __forceinline__ void pair_spatial(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+                                             const Geom& g, int s, const Pair& pr, H6<R>& acc) {
+  const int base = M_WP + 8 * I;
+  H6<R> h;
+  gather_pair<R, I == 0, I == 1, I == 2, 0>(psi, c, g, pr, h);
+  block2h<R, false>(W, s, base + 4 * pr.p, h, acc);
+  int n = gather_pair<R, -(I == 0), -(I == 1), -(I == 2), 0>(psi, c, g, pr, h);
+  block2h<R, true>(W, n, base + 4 * (1 - pr.p), h, acc);
+}
+
+// acc+ += S h+ - U l (p = 0);  acc- += -S h- + U l (p = 1)   [forward, matrices at x]
+// acc+ += -U^dag u - S^dag h+;  acc- += -U^dag u + S^dag h-   [backward, matrices at x - t]
+template <typename R>
+__device__ __forceinline__ void pair_time(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+                                          const Geom& g, int s, const Pair& pr, H6<R>& acc) {
+  const R sg = pr.p ? R(-1) : R(1);
+  H6<R> h, u, l;
+  gather_pair<R, 0, 0, 0, 1>(psi, c, g, pr, h, nullptr, &l);
+  {
+    // acc += sg (S h - U l),  S = [[s3, n1], [n2, -s3]]
+    H6<R> sh;
+    M3<R> s3 = wmat(W, s, M_ST + 0);
+    mv(sh.v[0], s3, h.v[0]);
+    mv(sh.v[1], s3, h.v[1]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sh.v[1][a] = -sh.v[1][a];
+    M3<R> n1 = wmat(W, s, M_ST + 1);
+    mv_add(sh.v[0], n1, h.v[1]);
+    M3<R> n2 = wmat(W, s, M_ST + 2);
+    mv_add(sh.v[1], n2, h.v[0]);
+    M3<R> U = wmat(W, s, M_UT);
+    mv_sub(sh.v[0], U, l.v[0]);
+    mv_sub(sh.v[1], U, l.v[1]);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        acc.v[q][a].re = fma(sg, sh.v[q][a].re, acc.v[q][a].re);
+        acc.v[q][a].im = fma(sg, sh.v[q][a].im, acc.v[q][a].im);
+      }
+  }
+  int n = gather_pair<R, 0, 0, 0, -1>(psi, c, g, pr, h, &u, nullptr);
+  {
+    // S^dag h = [[s3^dag, n2^dag], [n1^dag, -s3^dag]] h ; acc += -U^dag u - sg S^dag h
+    H6<R> sh;
+    M3<R> s3 = wmat(W, n, M_ST + 0);
+    mdv(sh.v[0], s3, h.v[0]);
+    mdv(sh.v[1], s3, h.v[1]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sh.v[1][a] = -sh.v[1][a];
+    M3<R> n2 = wmat(W, n, M_ST + 2);
+    mdv_add(sh.v[0], n2, h.v[1]);
+    M3<R> n1 = wmat(W, n, M_ST + 1);
+    mdv_add(sh.v[1], n1, h.v[0]);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        acc.v[q][a].re = fma(-sg, sh.v[q][a].re, acc.v[q][a].re);
+        acc.v[q][a].im = fma(-sg, sh.v[q][a].im, acc.v[q][a].im);
+      }
+    M3<R> U = wmat(W, n, M_UT);
+    mdv_sub(acc.v[0], U, u.v[0]);
+    mdv_sub(acc.v[1], U, u.v[1]);
+  }
+}
+
+// W^{++}_ii: acc+- += (a +- b sigma_i) V h+-  forward,  (a -+ b sigma_i) V^dag h+-  backward.
+template <typename R, int I>
+__device__ __forceinline__ void pair_two(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+                                         const Geom& g, int s, const Pair& pr, R a, R b, H6<R>& acc) {
+  const R sb = pr.p ? -b : b;
+  H6<R> h, y;
+  gather_pair<R, 2 * (I == 0), 2 * (I == 1), 2 * (I == 2), 0>(psi, c, g, pr, h);
+  M3<R> V = wmat(W, s, M_VII + I);
+  colour2h<R, false>(y, V, h);
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc.v[q][k].re = fma(a, y.v[q][k].re, acc.v[q][k].re);
+      acc.v[q][k].im = fma(a, y.v[q][k].im, acc.v[q][k].im);
+    }
+  add_sigma_h(acc, I, y, sb);
+  int n = gather_pair<R, -2 * (I == 0), -2 * (I == 1), -2 * (I == 2), 0>(psi, c, g, pr, h);
+  V = wmat(W, n, M_VII + I);
+  colour2h<R, true>(y, V, h);
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc.v[q][k].re = fma(a, y.v[q][k].re, acc.v[q][k].re);
+      acc.v[q][k].im = fma(a, y.v[q][k].im, acc.v[q][k].im);
+    }
+  add_sigma_h(acc, I, y, -sb);
+}
+
+// Diagonal pair (I, J): acc+- += +-(s_I + s_J) V h, -+(s_I + s_J) V^dag h (x-I-J),
+//                       +-(s_I - s_J) X h (x+I-J), -+(s_I - s_J) X^dag h (x-I+J).
+template <typename R, int I, int J, int P>
+__device__ __forceinline__ void pair_diag(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+                                          const Geom& g, int s, const Pair& pr, H6<R>& acc) {
+  constexpr int A0 = (I == 0) + (J == 0), A1 = (I == 1) + (J == 1), A2 = (I == 2) + (J == 2);
+  constexpr int B0 = (I == 0) - (J == 0), B1 = (I == 1) - (J == 1), B2 = (I == 2) - (J == 2);
+  const R sg = pr.p ? R(-1) : R(1);
+  H6<R> h, y;
+  M3<R> V;
+  gather_pair<R, A0, A1, A2, 0>(psi, c, g, pr, h);
+  V = wmat(W, s, M_VIJ + P);
+  colour2h<R, false>(y, V, h); add_sigma_h(acc, I, y, sg); add_sigma_h(acc, J, y, sg);
+  int n = gather_pair<R, -A0, -A1, -A2, 0>(psi, c, g, pr, h);
+  V = wmat(W, n, M_VIJ + P);
+  colour2h<R, true>(y, V, h); add_sigma_h(acc, I, y, -sg); add_sigma_h(acc, J, y, -sg);
+  gather_pair<R, B0, B1, B2, 0>(psi, c, g, pr, h);
+  V = wmat(W, s, M_XIJ + P);
+  colour2h<R, false>(y, V, h); add_sigma_h(acc, I, y, sg); add_sigma_h(acc, J, y, -sg);
+  n = gather_pair<R, -B0, -B1, -B2, 0>(psi, c, g, pr, h);
+  V = wmat(W, n, M_XIJ + P);
+  colour2h<R, true>(y, V, h); add_sigma_h(acc, I, y, -sg); add_sigma_h(acc, J, y, sg);
+}
+
+#ifndef OK_APPLY_MINB
+#define OK_APPLY_MINB 1
+#endif
+
+template <typename R, int EPI>
+__global__ void __launch_bounds__(APPLY_THREADS, OK_APPLY_MINB) apply_pair_kernel(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi,
+                                                                   cx<R>* __restrict__ out, Geom g, R c0q, R a_ii, R b_ii,
+                                                                   EpiArgs<R> ep) {
+  if (EPI != EPI_NONE && ep.halt && *ep.halt) return;
+  const int tid = blockIdx.x * APPLY_THREADS + threadIdx.x;
+  const int s = tid >> 1;
+  Pair pr;
+  pr.p = threadIdx.x & 1;
+  pr.mask = 3u << (threadIdx.x & 30);
+  double red[3] = {0.0, 0.0, 0.0};
+  if (s < g.V) {
+    int c[4];
+    {
+      int r = s;
+      c[0] = r % g.L[0]; r /= g.L[0];
+      c[1] = r % g.L[1]; r /= g.L[1];
+      c[2] = r % g.L[2]; c[3] = r / g.L[2];
+    }
+    H6<R> acc;
+    {
+      // on-site: p = 0 forms A = Y+ (u - i l), p = 1 forms B = Y- (u + i l); acc = (A + B) + i (A - B)
+      // for p = 0 and (A + B) - i (A - B) for p = 1, i.e. acc = (R + Rp) + i (R - Rp) for both.
+      H6<R> mine, oth, v, Rm;
+      load_half<R>(psi, s, pr.p, mine);
+      oth = partner(mine, pr.mask);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          cx<R> u = pr.p ? oth.v[q][k] : mine.v[q][k];
+          cx<R> l = pr.p ? mine.v[q][k] : oth.v[q][k];
+          v.v[q][k] = pr.p ? u + ti(l) : u - ti(l);
+          Rm.v[q][k] = c0q * v.v[q][k];
+        }
+      const int m0 = pr.p ? M_Y0M : M_Y0P;
+      M3<R> y = wmat(W, s, m0 + 0);
+      mv_add(Rm.v[0], y, v.v[0]); mv_sub(Rm.v[1], y, v.v[1]);
+      y = wmat(W, s, m0 + 1);
+      mv_add(Rm.v[0], y, v.v[1]);
+      y = wmat(W, s, m0 + 2);
+      mv_add(Rm.v[1], y, v.v[0]);
+      H6<R> Rp = partner(Rm, pr.mask);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc.v[q][k] = (Rm.v[q][k] + Rp.v[q][k]) + ti(Rm.v[q][k] - Rp.v[q][k]);
+    }
+    pair_spatial<R, 0>(W, psi, c, g, s, pr, acc);
+    pair_spatial<R, 1>(W, psi, c, g, s, pr, acc);
+    pair_spatial<R, 2>(W, psi, c, g, s, pr, acc);
+    pair_time<R>(W, psi, c, g, s, pr, acc);
+    pair_two<R, 0>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
+    pair_two<R, 1>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
+    pair_two<R, 2>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
+    pair_diag<R, 0, 1, 0>(W, psi, c, g, s, pr, acc);
+    pair_diag<R, 0, 2, 1>(W, psi, c, g, s, pr, acc);
+    pair_diag<R, 1, 2, 2>(W, psi, c, g, s, pr, acc);
+
+    // out_u = acc+ + acc- (p = 0 writes it), out_l = acc+ - acc- (p = 1)
+    H6<R> ap = partner(acc, pr.mask), o;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) o.v[q][k] = pr.p ? ap.v[q][k] - acc.v[q][k] : acc.v[q][k] + ap.v[q][k];
+    if (EPI == EPI_RESID) {
+      H6<R> bv;
+      load_half<R>(ep.b, s, pr.p, bv);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          o.v[q][k] = bv.v[q][k] - o.v[q][k];
+          red[0] += (double)o.v[q][k].re * o.v[q][k].re + (double)o.v[q][k].im * o.v[q][k].im;
+          red[1] += (double)bv.v[q][k].re * bv.v[q][k].re + (double)bv.v[q][k].im * bv.v[q][k].im;
+        }
+    }
+    store_half<R>(out, s, pr.p, o);
+    if (EPI == EPI_DOT) {
+      H6<R> rh;
+      load_half<R>(ep.rhat, s, pr.p, rh);
+      cx<R> d = mk<R>(0, 0);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d = fma_cj(rh.v[q][k], o.v[q][k], d);
+      red[0] = d.re;
+      red[1] = d.im;
+    } else if (EPI == EPI_TS) {
+      H6<R> x0;
+      load_half<R>(psi, s, pr.p, x0);
+      cx<R> d = mk<R>(0, 0);
+      R n2 = 0;
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          d = fma_cj(o.v[q][k], x0.v[q][k], d);
+          n2 += o.v[q][k].re * o.v[q][k].re + o.v[q][k].im * o.v[q][k].im;
+        }
+      red[0] = d.re;
+      red[1] = d.im;
+      red[2] = n2;
+    }
+  }
+  if (EPI == EPI_DOT || EPI == EPI_RESID) {
+    double v2[2] = {red[0], red[1]};
+    grid_reduce<2, APPLY_THREADS>(v2, ep.ra, ep.ticket);
+  } else if (EPI == EPI_TS) {
+    grid_reduce<3, APPLY_THREADS>(red, ep.ra, ep.ticket);
+  }
+}
+
 // ---------------------------------------------------------------------------- launchers
+// One thread per site for FP64 (bound by the FP64 pipe, where the pair's duplicated temporal
+// products cost more than the extra warps gain), two threads per site for FP32 (bound by memory).
+#ifndef OK_APPLY64_PAIR
+#define OK_APPLY64_PAIR 0
+#endif
+template <typename R> constexpr bool use_pair() { return sizeof(R) == 4 || OK_APPLY64_PAIR; }
+
 template <typename R>
 int launch_apply(const ok_W* Wh, const cx<R>* psi, cx<R>* out, int epi, const EpiArgs<R>& ep, cudaStream_t st) {
   const cx<R>* W = (const cx<R>*)(sizeof(R) == 8 ? Wh->W64 : Wh->W32);
   if (!W) return OK_EINVAL;
   const Geom& g = Wh->g;
+  if (use_pair<R>()) {
+    int nb = grid_for(2LL * g.V, APPLY_THREADS);
+    R c0q = (R)Wh->sc.c0q, a = (R)Wh->sc.a_ii, b = (R)Wh->sc.b_ii;
+    static const char* n64[4] = {"apply_f64", "apply_f64_dot", "apply_f64_ts", "apply_f64_resid"};
+    static const char* n32[4] = {"apply_f32", "apply_f32_dot", "apply_f32_ts", "apply_f32_resid"};
+    if (epi < EPI_NONE || epi > EPI_RESID) return OK_EINVAL;
+    {
+      TraceScope ts(sizeof(R) == 8 ? n64[epi] : n32[epi], st);
+      switch (epi) {
+        case EPI_NONE: apply_pair_kernel<R, EPI_NONE><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+        case EPI_DOT: apply_pair_kernel<R, EPI_DOT><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+        case EPI_TS: apply_pair_kernel<R, EPI_TS><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+        default: apply_pair_kernel<R, EPI_RESID><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+      }
+    }
+    OK_LAUNCH_CHECK();
+    return OK_SUCCESS;
+  }
   int nb = grid_for(g.V, APPLY_THREADS);
   R c0q = (R)Wh->sc.c0q, a = (R)Wh->sc.a_ii, b = (R)Wh->sc.b_ii;
   static const char* names64[4] = {"apply_f64", "apply_f64_dot", "apply_f64_ts", "apply_f64_resid"};
@@ -470,7 +865,7 @@ int launch_apply(const ok_W* Wh, const cx<R>* psi, cx<R>* out, int epi, const Ep
   return OK_SUCCESS;
 }
 
-int apply_blocks_needed(const ok_W* Wh) { return grid_for(Wh->g.V, APPLY_THREADS); }
+int apply_blocks_needed(const ok_W* Wh) { return grid_for(2LL * Wh->g.V, APPLY_THREADS); }
 
 template int launch_apply<double>(const ok_W*, const cx<double>*, cx<double>*, int, const EpiArgs<double>&, cudaStream_t);
 template int launch_apply<float>(const ok_W*, const cx<float>*, cx<float>*, int, const EpiArgs<float>&, cudaStream_t);

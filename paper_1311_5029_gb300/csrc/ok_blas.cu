@@ -167,6 +167,18 @@ __global__ void __launch_bounds__(BLAS_THREADS) accum_x_kernel(double2* __restri
   }
 }
 
+// <x, x> and <b, b> (FP64 vectors, complex-double units).
+__global__ void __launch_bounds__(BLAS_THREADS) norms_kernel(const double2* __restrict__ x, const double2* __restrict__ b,
+                                                             long long n, SolverState* __restrict__ st, RedArgs ra) {
+  double red[2] = {0.0, 0.0};
+  OK_GRID_STRIDE(i, n) {
+    double2 u = x[i], v = b[i];
+    red[0] += u.x * u.x + u.y * u.y;
+    red[1] += v.x * v.x + v.y * v.y;
+  }
+  grid_reduce<2, BLAS_THREADS>(red, ra, &st->ticket[6]);
+}
+
 // ---------------------------------------------------------------------------- launchers
 static int g_sms = 0;
 
@@ -259,6 +271,16 @@ int launch_accum_x(cx<double>* x64, cx<float>* x32, long long n, cudaStream_t st
   {
     TraceScope ts("accum_x", strm);
     accum_x_kernel<<<blas_blocks(n), BLAS_THREADS, 0, strm>>>((double2*)x64, (float2*)x32, n);
+  }
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+int launch_norms(const cx<double>* x, const cx<double>* b, long long n, SolverState* st, double* part, cudaStream_t strm) {
+  RedArgs ra{st, part, nullptr, FIN_RESID};
+  {
+    TraceScope ts("norms_f64", strm);
+    norms_kernel<<<blas_blocks(n), BLAS_THREADS, 0, strm>>>((const double2*)x, (const double2*)b, n, st, ra);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;

@@ -124,9 +124,9 @@ ok_solve_params ok_default_solve_params(double tol, int maxiter) {
   p.tol = tol;
   p.maxiter = maxiter;
   p.mode = OK_SOLVE_AUTO;
-  p.delta = 0.1;
+  p.delta = 1e-3;
   p.max_restarts = 5;
-  p.check_every = 8;
+  p.check_every = 4;
   return p;
 }
 

@@ -38,6 +38,8 @@ int launch_restart(const cx<R>* r, cx<R>* rhat, cx<R>* p, long long n, SolverSta
 int launch_demote(const cx<double>* r64, cx<float>* r32, cx<float>* rhat, cx<float>* p, long long n, bool restart,
                   SolverState* st, double* part, cudaStream_t strm);
 int launch_accum_x(cx<double>* x64, cx<float>* x32, long long n, cudaStream_t strm);
+// <x, x> and <b, b> in FP64 -> FIN_RESID (state bb = <b, b>, aux = the two sums)
+int launch_norms(const cx<double>* x, const cx<double>* b, long long n, SolverState* st, double* part, cudaStream_t strm);
 
 // ok_precompute.cu
 int geom_from_lattice(const ok_lattice* lat, Geom* g);

@@ -153,9 +153,17 @@ int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solv
     return rc;
   };
 
-  // r = b - M x (FP64), then start the iteration from it.
-  OK_TRY(residual64(W, bvec, x, r64, dst, part, st));
-  inf.fp64_applies++;
+  // r = b - M x (FP64), then start the iteration from it.  A zero initial guess (checked with one
+  // pass over x and b) gives r = b without applying M.
+  OK_TRY(launch_norms(x, bvec, n, dst, part, st));
+  OK_TRY(read_state(dst, h, st));
+  if (h->aux[0] == 0.0) {
+    OK_CUDA_TRY(cudaMemcpyAsync(r64, bvec, n * sizeof(cx<double>), cudaMemcpyDeviceToDevice, st));
+    h->aux[0] = h->bb;
+  } else {
+    OK_TRY(residual64(W, bvec, x, r64, dst, part, st));
+    inf.fp64_applies++;
+  }
   if (mode == OK_SOLVE_F64) OK_TRY(launch_restart<double>(r64, b64.rhat, b64.p, n, dst, part, st));
   else OK_TRY(launch_demote(r64, b32.r, b32.rhat, b32.p, n, true, dst, part, st));
   OK_TRY(read_state(dst, h, st));

@@ -61,7 +61,7 @@ def test_null_arguments_are_rejected(lib):
 
 def test_default_solve_params(lib):
     p = lib.ok_default_solve_params(1e-9, 77)
-    assert (p.tol, p.maxiter, p.mode, p.delta, p.max_restarts, p.check_every) == (1e-9, 77, 0, 0.1, 5, 8)
+    assert (p.tol, p.maxiter, p.mode, p.delta, p.max_restarts, p.check_every) == (1e-9, 77, 0, 1e-3, 5, 4)
 
 
 def test_binding_rejects_host_tensors(lib):
