@@ -1,0 +1,61 @@
+"""Host logic of bench.py without a GPU: byte accounting and the max/sum aggregation over ranks
+(two gloo ranks on the CPU, the path bench.py takes under torchrun)."""
+import multiprocessing as mp
+import os
+import socket
+
+import pytest
+
+import bench
+
+
+def test_byte_model():
+    assert bench.APPLY32 == 3288 and bench.APPLY64 == 6576
+    assert bench.W32_BYTES == 43 * 9 * 8
+    info = dict(iters=10, fp64_applies=2, reliable_updates=1, restarts=0)
+    V = 1000
+    expect = V * (10 * (2 * 3288 + bench.ITER_VEC32) + 2 * bench.RESID64 + 2 * bench.RELIABLE32)
+    assert bench.solve_bytes(V, info, "mixed") == expect
+    assert bench.solve_bytes(V, dict(iters=0, fp64_applies=0, reliable_updates=0, restarts=0), "f64") == \
+        V * bench.RESTART64
+
+
+def test_reduce_without_process_group():
+    assert bench.reduce_max_sum(3.0, 7.0) == (3.0, 7.0)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    import bench as b
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        t, u = b.reduce_max_sum(10.0 + rank, 100.0 * (rank + 1))
+        b.barrier()
+        q.put((rank, t, u))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.timeout(120)
+def test_two_rank_max_time_sum_units():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=100) for _ in procs)
+    for p in procs:
+        p.join(timeout=30)
+        assert p.exitcode == 0
+    assert out == [(0, 11.0, 300.0), (1, 11.0, 300.0)]
