@@ -577,26 +577,32 @@ __device__ __forceinline__ void colour2h(H6<R>& y, const M3<R>& V, const H6<R>& 
   else { mv(y.v[0], V, h.v[0]); mv(y.v[1], V, h.v[1]); }
 }
 
-template <typename R, int I>
+// Each hop function takes FWD / BWD flags so that the forward and the backward halves of the
+// stencil can run in different warps (the split kernel below).
+template <typename R, int I, bool FWD = true, bool BWD = true>
 __device__ __forceinline__ void pair_spatial(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
                                              const Geom& g, int s, const Pair& pr, H6<R>& acc) {
   const int base = M_WP + 8 * I;
   H6<R> h;
-  gather_pair<R, I == 0, I == 1, I == 2, 0>(psi, c, g, pr, h);
-  block2h<R, false>(W, s, base + 4 * pr.p, h, acc);
-  int n = gather_pair<R, -(I == 0), -(I == 1), -(I == 2), 0>(psi, c, g, pr, h);
-  block2h<R, true>(W, n, base + 4 * (1 - pr.p), h, acc);
+  if constexpr (FWD) {
+    gather_pair<R, I == 0, I == 1, I == 2, 0>(psi, c, g, pr, h);
+    block2h<R, false>(W, s, base + 4 * pr.p, h, acc);
+  }
+  if constexpr (BWD) {
+    int n = gather_pair<R, -(I == 0), -(I == 1), -(I == 2), 0>(psi, c, g, pr, h);
+    block2h<R, true>(W, n, base + 4 * (1 - pr.p), h, acc);
+  }
 }
 
 // acc+ += S h+ - U l (p = 0);  acc- += -S h- + U l (p = 1)   [forward, matrices at x]
 // acc+ += -U^dag u - S^dag h+;  acc- += -U^dag u + S^dag h-   [backward, matrices at x - t]
-template <typename R>
+template <typename R, bool FWD = true, bool BWD = true>
 __device__ __forceinline__ void pair_time(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
                                           const Geom& g, int s, const Pair& pr, H6<R>& acc) {
   const R sg = pr.p ? R(-1) : R(1);
   H6<R> h, u, l;
-  gather_pair<R, 0, 0, 0, 1>(psi, c, g, pr, h, nullptr, &l);
-  {
+  if constexpr (FWD) {
+    gather_pair<R, 0, 0, 0, 1>(psi, c, g, pr, h, nullptr, &l);
     // acc += sg (S h - U l),  S = [[s3, n1], [n2, -s3]]
     H6<R> sh;
     M3<R> s3 = wmat(W, s, M_ST + 0);
@@ -619,8 +625,8 @@ __device__ __forceinline__ void pair_time(const cx<R>* __restrict__ W, const cx<
         acc.v[q][a].im = fma(sg, sh.v[q][a].im, acc.v[q][a].im);
       }
   }
-  int n = gather_pair<R, 0, 0, 0, -1>(psi, c, g, pr, h, &u, nullptr);
-  {
+  if constexpr (BWD) {
+    int n = gather_pair<R, 0, 0, 0, -1>(psi, c, g, pr, h, &u, nullptr);
     // S^dag h = [[s3^dag, n2^dag], [n1^dag, -s3^dag]] h ; acc += -U^dag u - sg S^dag h
     H6<R> sh;
     M3<R> s3 = wmat(W, n, M_ST + 0);
@@ -645,39 +651,42 @@ __device__ __forceinline__ void pair_time(const cx<R>* __restrict__ W, const cx<
   }
 }
 
+template <typename R>
+__device__ __forceinline__ void add_scaled_h(H6<R>& acc, R a, const H6<R>& y) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc.v[q][k].re = fma(a, y.v[q][k].re, acc.v[q][k].re);
+      acc.v[q][k].im = fma(a, y.v[q][k].im, acc.v[q][k].im);
+    }
+}
+
 // W^{++}_ii: acc+- += (a +- b sigma_i) V h+-  forward,  (a -+ b sigma_i) V^dag h+-  backward.
-template <typename R, int I>
+template <typename R, int I, bool FWD = true, bool BWD = true>
 __device__ __forceinline__ void pair_two(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
                                          const Geom& g, int s, const Pair& pr, R a, R b, H6<R>& acc) {
   const R sb = pr.p ? -b : b;
   H6<R> h, y;
-  gather_pair<R, 2 * (I == 0), 2 * (I == 1), 2 * (I == 2), 0>(psi, c, g, pr, h);
-  M3<R> V = wmat(W, s, M_VII + I);
-  colour2h<R, false>(y, V, h);
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      acc.v[q][k].re = fma(a, y.v[q][k].re, acc.v[q][k].re);
-      acc.v[q][k].im = fma(a, y.v[q][k].im, acc.v[q][k].im);
-    }
-  add_sigma_h(acc, I, y, sb);
-  int n = gather_pair<R, -2 * (I == 0), -2 * (I == 1), -2 * (I == 2), 0>(psi, c, g, pr, h);
-  V = wmat(W, n, M_VII + I);
-  colour2h<R, true>(y, V, h);
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      acc.v[q][k].re = fma(a, y.v[q][k].re, acc.v[q][k].re);
-      acc.v[q][k].im = fma(a, y.v[q][k].im, acc.v[q][k].im);
-    }
-  add_sigma_h(acc, I, y, -sb);
+  if constexpr (FWD) {
+    gather_pair<R, 2 * (I == 0), 2 * (I == 1), 2 * (I == 2), 0>(psi, c, g, pr, h);
+    M3<R> V = wmat(W, s, M_VII + I);
+    colour2h<R, false>(y, V, h);
+    add_scaled_h(acc, a, y);
+    add_sigma_h(acc, I, y, sb);
+  }
+  if constexpr (BWD) {
+    int n = gather_pair<R, -2 * (I == 0), -2 * (I == 1), -2 * (I == 2), 0>(psi, c, g, pr, h);
+    M3<R> V = wmat(W, n, M_VII + I);
+    colour2h<R, true>(y, V, h);
+    add_scaled_h(acc, a, y);
+    add_sigma_h(acc, I, y, -sb);
+  }
 }
 
 // Diagonal pair (I, J): acc+- += +-(s_I + s_J) V h, -+(s_I + s_J) V^dag h (x-I-J),
 //                       +-(s_I - s_J) X h (x+I-J), -+(s_I - s_J) X^dag h (x-I+J).
-template <typename R, int I, int J, int P>
+template <typename R, int I, int J, int P, bool FWD = true, bool BWD = true>
 __device__ __forceinline__ void pair_diag(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
                                           const Geom& g, int s, const Pair& pr, H6<R>& acc) {
   constexpr int A0 = (I == 0) + (J == 0), A1 = (I == 1) + (J == 1), A2 = (I == 2) + (J == 2);
@@ -685,18 +694,22 @@ __device__ __forceinline__ void pair_diag(const cx<R>* __restrict__ W, const cx<
   const R sg = pr.p ? R(-1) : R(1);
   H6<R> h, y;
   M3<R> V;
-  gather_pair<R, A0, A1, A2, 0>(psi, c, g, pr, h);
-  V = wmat(W, s, M_VIJ + P);
-  colour2h<R, false>(y, V, h); add_sigma_h(acc, I, y, sg); add_sigma_h(acc, J, y, sg);
-  int n = gather_pair<R, -A0, -A1, -A2, 0>(psi, c, g, pr, h);
-  V = wmat(W, n, M_VIJ + P);
-  colour2h<R, true>(y, V, h); add_sigma_h(acc, I, y, -sg); add_sigma_h(acc, J, y, -sg);
-  gather_pair<R, B0, B1, B2, 0>(psi, c, g, pr, h);
-  V = wmat(W, s, M_XIJ + P);
-  colour2h<R, false>(y, V, h); add_sigma_h(acc, I, y, sg); add_sigma_h(acc, J, y, -sg);
-  n = gather_pair<R, -B0, -B1, -B2, 0>(psi, c, g, pr, h);
-  V = wmat(W, n, M_XIJ + P);
-  colour2h<R, true>(y, V, h); add_sigma_h(acc, I, y, -sg); add_sigma_h(acc, J, y, sg);
+  if constexpr (FWD) {
+    gather_pair<R, A0, A1, A2, 0>(psi, c, g, pr, h);
+    V = wmat(W, s, M_VIJ + P);
+    colour2h<R, false>(y, V, h); add_sigma_h(acc, I, y, sg); add_sigma_h(acc, J, y, sg);
+    gather_pair<R, B0, B1, B2, 0>(psi, c, g, pr, h);
+    V = wmat(W, s, M_XIJ + P);
+    colour2h<R, false>(y, V, h); add_sigma_h(acc, I, y, sg); add_sigma_h(acc, J, y, -sg);
+  }
+  if constexpr (BWD) {
+    int n = gather_pair<R, -A0, -A1, -A2, 0>(psi, c, g, pr, h);
+    V = wmat(W, n, M_VIJ + P);
+    colour2h<R, true>(y, V, h); add_sigma_h(acc, I, y, -sg); add_sigma_h(acc, J, y, -sg);
+    n = gather_pair<R, -B0, -B1, -B2, 0>(psi, c, g, pr, h);
+    V = wmat(W, n, M_XIJ + P);
+    colour2h<R, true>(y, V, h); add_sigma_h(acc, I, y, -sg); add_sigma_h(acc, J, y, sg);
+  }
 }
 
 #ifndef OK_APPLY_MINB
@@ -816,56 +829,207 @@ __global__ void __launch_bounds__(APPLY_THREADS, OK_APPLY_MINB) apply_pair_kerne
   }
 }
 
-// ---------------------------------------------------------------------------- launchers
-// One thread per site for FP64 (bound by the FP64 pipe, where the pair's duplicated temporal
-// products cost more than the extra warps gain), two threads per site for FP32 (bound by memory).
-#ifndef OK_APPLY64_PAIR
-#define OK_APPLY64_PAIR 0
+// ============================================================================ split kernel
+// A block of 128 threads covers 32 sites.  Warps 0-1 (thread pairs as above) do the on-site term
+// and the 13 forward hops, warps 2-3 the 13 backward hops of the same sites; the backward half
+// hands its partial sums over through shared memory.  Each thread's chain of dependent
+// load-then-multiply rounds is half as long as in the pair kernel, so twice as many global loads
+// are in flight per resident site.
+constexpr int SPLIT_THREADS = 128;
+constexpr int SPLIT_SITES = 32;
+
+// 4 resident blocks per SM (128 registers per thread): measured best on 16^3 x 32 (102 us against
+// 119 us with 2 blocks and 117 us with 5).
+#ifndef OK_SPLIT_MINB
+#define OK_SPLIT_MINB 4
 #endif
-template <typename R> constexpr bool use_pair() { return sizeof(R) == 4 || OK_APPLY64_PAIR; }
+
+template <typename R, int EPI>
+__global__ void __launch_bounds__(SPLIT_THREADS, OK_SPLIT_MINB) apply_split_kernel(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi,
+                                                                                   cx<R>* __restrict__ out, Geom g, R c0q, R a_ii, R b_ii,
+                                                                                   EpiArgs<R> ep) {
+  if (EPI != EPI_NONE && ep.halt && *ep.halt) return;
+  __shared__ cx<R> xch[64][6];
+  const int half = threadIdx.x >> 6;  // warp-uniform: 0 forward, 1 backward
+  const int t = threadIdx.x & 63;
+  const int s = blockIdx.x * SPLIT_SITES + (t >> 1);
+  Pair pr;
+  pr.p = t & 1;
+  pr.mask = 3u << (threadIdx.x & 30);
+  const bool active = s < g.V;
+  double red[3] = {0.0, 0.0, 0.0};
+  H6<R> acc;
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc.v[q][k] = mk<R>(0, 0);
+  int c[4] = {0, 0, 0, 0};
+  if (active) {
+    int r = s;
+    c[0] = r % g.L[0]; r /= g.L[0];
+    c[1] = r % g.L[1]; r /= g.L[1];
+    c[2] = r % g.L[2]; c[3] = r / g.L[2];
+    if (half == 0) {
+      H6<R> mine, oth, v, Rm;
+      load_half<R>(psi, s, pr.p, mine);
+      oth = partner(mine, pr.mask);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          cx<R> u = pr.p ? oth.v[q][k] : mine.v[q][k];
+          cx<R> l = pr.p ? mine.v[q][k] : oth.v[q][k];
+          v.v[q][k] = pr.p ? u + ti(l) : u - ti(l);
+          Rm.v[q][k] = c0q * v.v[q][k];
+        }
+      const int m0 = pr.p ? M_Y0M : M_Y0P;
+      M3<R> y = wmat(W, s, m0 + 0);
+      mv_add(Rm.v[0], y, v.v[0]); mv_sub(Rm.v[1], y, v.v[1]);
+      y = wmat(W, s, m0 + 1);
+      mv_add(Rm.v[0], y, v.v[1]);
+      y = wmat(W, s, m0 + 2);
+      mv_add(Rm.v[1], y, v.v[0]);
+      H6<R> Rp = partner(Rm, pr.mask);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc.v[q][k] = (Rm.v[q][k] + Rp.v[q][k]) + ti(Rm.v[q][k] - Rp.v[q][k]);
+      pair_spatial<R, 0, true, false>(W, psi, c, g, s, pr, acc);
+      pair_spatial<R, 1, true, false>(W, psi, c, g, s, pr, acc);
+      pair_spatial<R, 2, true, false>(W, psi, c, g, s, pr, acc);
+      pair_time<R, true, false>(W, psi, c, g, s, pr, acc);
+      pair_two<R, 0, true, false>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_two<R, 1, true, false>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_two<R, 2, true, false>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_diag<R, 0, 1, 0, true, false>(W, psi, c, g, s, pr, acc);
+      pair_diag<R, 0, 2, 1, true, false>(W, psi, c, g, s, pr, acc);
+      pair_diag<R, 1, 2, 2, true, false>(W, psi, c, g, s, pr, acc);
+    } else {
+      pair_spatial<R, 0, false, true>(W, psi, c, g, s, pr, acc);
+      pair_spatial<R, 1, false, true>(W, psi, c, g, s, pr, acc);
+      pair_spatial<R, 2, false, true>(W, psi, c, g, s, pr, acc);
+      pair_time<R, false, true>(W, psi, c, g, s, pr, acc);
+      pair_two<R, 0, false, true>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_two<R, 1, false, true>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_two<R, 2, false, true>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_diag<R, 0, 1, 0, false, true>(W, psi, c, g, s, pr, acc);
+      pair_diag<R, 0, 2, 1, false, true>(W, psi, c, g, s, pr, acc);
+      pair_diag<R, 1, 2, 2, false, true>(W, psi, c, g, s, pr, acc);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) xch[t][3 * q + k] = acc.v[q][k];
+    }
+  }
+  __syncthreads();
+  if (half == 0 && active) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc.v[q][k] = acc.v[q][k] + xch[t][3 * q + k];
+    // out_u = acc+ + acc- (p = 0 writes it), out_l = acc+ - acc- (p = 1)
+    H6<R> ap = partner(acc, pr.mask), o;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) o.v[q][k] = pr.p ? ap.v[q][k] - acc.v[q][k] : acc.v[q][k] + ap.v[q][k];
+    if (EPI == EPI_RESID) {
+      H6<R> bv;
+      load_half<R>(ep.b, s, pr.p, bv);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          o.v[q][k] = bv.v[q][k] - o.v[q][k];
+          red[0] += (double)o.v[q][k].re * o.v[q][k].re + (double)o.v[q][k].im * o.v[q][k].im;
+          red[1] += (double)bv.v[q][k].re * bv.v[q][k].re + (double)bv.v[q][k].im * bv.v[q][k].im;
+        }
+    }
+    store_half<R>(out, s, pr.p, o);
+    if (EPI == EPI_DOT) {
+      H6<R> rh;
+      load_half<R>(ep.rhat, s, pr.p, rh);
+      cx<R> d = mk<R>(0, 0);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d = fma_cj(rh.v[q][k], o.v[q][k], d);
+      red[0] = d.re;
+      red[1] = d.im;
+    } else if (EPI == EPI_TS) {
+      H6<R> x0;
+      load_half<R>(psi, s, pr.p, x0);
+      cx<R> d = mk<R>(0, 0);
+      R n2 = 0;
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          d = fma_cj(o.v[q][k], x0.v[q][k], d);
+          n2 += o.v[q][k].re * o.v[q][k].re + o.v[q][k].im * o.v[q][k].im;
+        }
+      red[0] = d.re;
+      red[1] = d.im;
+      red[2] = n2;
+    }
+  }
+  if (EPI == EPI_DOT || EPI == EPI_RESID) {
+    double v2[2] = {red[0], red[1]};
+    grid_reduce<2, SPLIT_THREADS>(v2, ep.ra, ep.ticket);
+  } else if (EPI == EPI_TS) {
+    grid_reduce<3, SPLIT_THREADS>(red, ep.ra, ep.ticket);
+  }
+}
+
+// ---------------------------------------------------------------------------- launchers
+// Kernel variant per precision: 0 = one thread per site, 1 = thread pair per site, 2 = split
+// (forward and backward halves in different warps).  FP64 is bound by the FP64 pipe, where one
+// thread per site does the least arithmetic; FP32 is bound by memory latency, where the split
+// kernel keeps the most loads in flight.
+#ifndef OK_APPLY64_VARIANT
+#define OK_APPLY64_VARIANT 0
+#endif
+#ifndef OK_APPLY32_VARIANT
+#define OK_APPLY32_VARIANT 2
+#endif
+template <typename R> constexpr int apply_variant() { return sizeof(R) == 8 ? OK_APPLY64_VARIANT : OK_APPLY32_VARIANT; }
+
+template <typename R, int EPI>
+static void launch_variant(const cx<R>* W, const cx<R>* psi, cx<R>* out, const Geom& g, R c0q, R a, R b,
+                           const EpiArgs<R>& ep, cudaStream_t st) {
+  constexpr int v = apply_variant<R>();
+  if constexpr (v == 2)
+    apply_split_kernel<R, EPI><<<grid_for(g.V, SPLIT_SITES), SPLIT_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep);
+  else if constexpr (v == 1)
+    apply_pair_kernel<R, EPI><<<grid_for(2LL * g.V, APPLY_THREADS), APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep);
+  else
+    apply_kernel<R, EPI><<<grid_for(g.V, APPLY_THREADS), APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep);
+}
 
 template <typename R>
 int launch_apply(const ok_W* Wh, const cx<R>* psi, cx<R>* out, int epi, const EpiArgs<R>& ep, cudaStream_t st) {
   const cx<R>* W = (const cx<R>*)(sizeof(R) == 8 ? Wh->W64 : Wh->W32);
   if (!W) return OK_EINVAL;
-  const Geom& g = Wh->g;
-  if (use_pair<R>()) {
-    int nb = grid_for(2LL * g.V, APPLY_THREADS);
-    R c0q = (R)Wh->sc.c0q, a = (R)Wh->sc.a_ii, b = (R)Wh->sc.b_ii;
-    static const char* n64[4] = {"apply_f64", "apply_f64_dot", "apply_f64_ts", "apply_f64_resid"};
-    static const char* n32[4] = {"apply_f32", "apply_f32_dot", "apply_f32_ts", "apply_f32_resid"};
-    if (epi < EPI_NONE || epi > EPI_RESID) return OK_EINVAL;
-    {
-      TraceScope ts(sizeof(R) == 8 ? n64[epi] : n32[epi], st);
-      switch (epi) {
-        case EPI_NONE: apply_pair_kernel<R, EPI_NONE><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-        case EPI_DOT: apply_pair_kernel<R, EPI_DOT><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-        case EPI_TS: apply_pair_kernel<R, EPI_TS><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-        default: apply_pair_kernel<R, EPI_RESID><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-      }
-    }
-    OK_LAUNCH_CHECK();
-    return OK_SUCCESS;
-  }
-  int nb = grid_for(g.V, APPLY_THREADS);
-  R c0q = (R)Wh->sc.c0q, a = (R)Wh->sc.a_ii, b = (R)Wh->sc.b_ii;
-  static const char* names64[4] = {"apply_f64", "apply_f64_dot", "apply_f64_ts", "apply_f64_resid"};
-  static const char* names32[4] = {"apply_f32", "apply_f32_dot", "apply_f32_ts", "apply_f32_resid"};
   if (epi < EPI_NONE || epi > EPI_RESID) return OK_EINVAL;
+  const Geom& g = Wh->g;
+  R c0q = (R)Wh->sc.c0q, a = (R)Wh->sc.a_ii, b = (R)Wh->sc.b_ii;
+  static const char* n64[4] = {"apply_f64", "apply_f64_dot", "apply_f64_ts", "apply_f64_resid"};
+  static const char* n32[4] = {"apply_f32", "apply_f32_dot", "apply_f32_ts", "apply_f32_resid"};
   {
-    TraceScope ts(sizeof(R) == 8 ? names64[epi] : names32[epi], st);
+    TraceScope ts(sizeof(R) == 8 ? n64[epi] : n32[epi], st);
     switch (epi) {
-      case EPI_NONE: apply_kernel<R, EPI_NONE><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-      case EPI_DOT: apply_kernel<R, EPI_DOT><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-      case EPI_TS: apply_kernel<R, EPI_TS><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-      default: apply_kernel<R, EPI_RESID><<<nb, APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+      case EPI_NONE: launch_variant<R, EPI_NONE>(W, psi, out, g, c0q, a, b, ep, st); break;
+      case EPI_DOT: launch_variant<R, EPI_DOT>(W, psi, out, g, c0q, a, b, ep, st); break;
+      case EPI_TS: launch_variant<R, EPI_TS>(W, psi, out, g, c0q, a, b, ep, st); break;
+      default: launch_variant<R, EPI_RESID>(W, psi, out, g, c0q, a, b, ep, st); break;
     }
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
 }
 
-int apply_blocks_needed(const ok_W* Wh) { return grid_for(2LL * Wh->g.V, APPLY_THREADS); }
+// Upper bound of the grid size of any apply variant (sizes the reduction partials).
+int apply_blocks_needed(const ok_W* Wh) { return grid_for(Wh->g.V, SPLIT_SITES); }
 
 template int launch_apply<double>(const ok_W*, const cx<double>*, cx<double>*, int, const EpiArgs<double>&, cudaStream_t);
 template int launch_apply<float>(const ok_W*, const cx<float>*, cx<float>*, int, const EpiArgs<float>&, cudaStream_t);
