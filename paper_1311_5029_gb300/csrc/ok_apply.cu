@@ -849,15 +849,22 @@ __global__ void __launch_bounds__(SPLIT_THREADS, OK_SPLIT_MINB) apply_split_kern
                                                                                    cx<R>* __restrict__ out, Geom g, R c0q, R a_ii, R b_ii,
                                                                                    EpiArgs<R> ep) {
   if (EPI != EPI_NONE && ep.halt && *ep.halt) return;
-  __shared__ cx<R> xch[64][6];
+  // Persistent: each block walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The hand-off buffer
+  // is double-buffered by tile parity, so one barrier per tile suffices: the backward half writes
+  // buffer k & 1 for tile k only after the barrier of tile k - 1, which the forward half passes
+  // only after it has read buffer (k - 2) & 1 = k & 1.
+  __shared__ cx<R> xch[2][64][6];
   const int half = threadIdx.x >> 6;  // warp-uniform: 0 forward, 1 backward
   const int t = threadIdx.x & 63;
-  const int s = blockIdx.x * SPLIT_SITES + (t >> 1);
   Pair pr;
   pr.p = t & 1;
   pr.mask = 3u << (threadIdx.x & 30);
-  const bool active = s < g.V;
   double red[3] = {0.0, 0.0, 0.0};
+  const int ntiles = (g.V + SPLIT_SITES - 1) / SPLIT_SITES;
+  int kb = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, kb ^= 1) {
+  const int s = tile * SPLIT_SITES + (t >> 1);
+  const bool active = s < g.V;
   H6<R> acc;
 #pragma unroll
   for (int q = 0; q < 2; ++q)
@@ -918,7 +925,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, OK_SPLIT_MINB) apply_split_kern
 #pragma unroll
       for (int q = 0; q < 2; ++q)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) xch[t][3 * q + k] = acc.v[q][k];
+        for (int k = 0; k < 3; ++k) xch[kb][t][3 * q + k] = acc.v[q][k];
     }
   }
   __syncthreads();
@@ -926,7 +933,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, OK_SPLIT_MINB) apply_split_kern
 #pragma unroll
     for (int q = 0; q < 2; ++q)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) acc.v[q][k] = acc.v[q][k] + xch[t][3 * q + k];
+      for (int k = 0; k < 3; ++k) acc.v[q][k] = acc.v[q][k] + xch[kb][t][3 * q + k];
     // out_u = acc+ + acc- (p = 0 writes it), out_l = acc+ - acc- (p = 1)
     H6<R> ap = partner(acc, pr.mask), o;
 #pragma unroll
@@ -954,8 +961,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, OK_SPLIT_MINB) apply_split_kern
       for (int q = 0; q < 2; ++q)
 #pragma unroll
         for (int k = 0; k < 3; ++k) d = fma_cj(rh.v[q][k], o.v[q][k], d);
-      red[0] = d.re;
-      red[1] = d.im;
+      red[0] += d.re;
+      red[1] += d.im;
     } else if (EPI == EPI_TS) {
       H6<R> x0;
       load_half<R>(psi, s, pr.p, x0);
@@ -968,11 +975,12 @@ __global__ void __launch_bounds__(SPLIT_THREADS, OK_SPLIT_MINB) apply_split_kern
           d = fma_cj(o.v[q][k], x0.v[q][k], d);
           n2 += o.v[q][k].re * o.v[q][k].re + o.v[q][k].im * o.v[q][k].im;
         }
-      red[0] = d.re;
-      red[1] = d.im;
-      red[2] = n2;
+      red[0] += d.re;
+      red[1] += d.im;
+      red[2] += n2;
     }
   }
+  }  // tiles
   if (EPI == EPI_DOT || EPI == EPI_RESID) {
     double v2[2] = {red[0], red[1]};
     grid_reduce<2, SPLIT_THREADS>(v2, ep.ra, ep.ticket);
@@ -998,8 +1006,11 @@ template <typename R, int EPI>
 static void launch_variant(const cx<R>* W, const cx<R>* psi, cx<R>* out, const Geom& g, R c0q, R a, R b,
                            const EpiArgs<R>& ep, cudaStream_t st) {
   constexpr int v = apply_variant<R>();
-  if constexpr (v == 2)
-    apply_split_kernel<R, EPI><<<grid_for(g.V, SPLIT_SITES), SPLIT_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep);
+  if constexpr (v == 2) {
+    const int tiles = grid_for(g.V, SPLIT_SITES);
+    const int resident = sm_count() * OK_SPLIT_MINB;
+    apply_split_kernel<R, EPI><<<tiles < resident ? tiles : resident, SPLIT_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep);
+  }
   else if constexpr (v == 1)
     apply_pair_kernel<R, EPI><<<grid_for(2LL * g.V, APPLY_THREADS), APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep);
   else

@@ -182,14 +182,18 @@ __global__ void __launch_bounds__(BLAS_THREADS) norms_kernel(const double2* __re
 // ---------------------------------------------------------------------------- launchers
 static int g_sms = 0;
 
-int blas_blocks(long long units) {
+int sm_count() {
   if (g_sms == 0) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 132;
     g_sms = sms;
   }
+  return g_sms;
+}
+
+int blas_blocks(long long units) {
   long long need = (units + BLAS_THREADS - 1) / BLAS_THREADS;
-  long long cap = (long long)g_sms * 8;
+  long long cap = (long long)sm_count() * 8;
   return (int)(need < cap ? (need > 0 ? need : 1) : cap);
 }
 

@@ -26,6 +26,7 @@ int launch_apply(const ok_W* W, const cx<R>* psi, cx<R>* out, int epi, const Epi
 int apply_blocks_needed(const ok_W* W);
 
 int blas_blocks(long long units);
+int sm_count();  // multiprocessors of the current device (cached)
 template <typename R>
 int launch_update_s(const cx<R>* r, const cx<R>* v, cx<R>* s, long long n, const SolverState* st, cudaStream_t strm);
 template <typename R>

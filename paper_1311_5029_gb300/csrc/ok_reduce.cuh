@@ -175,12 +175,25 @@ __device__ __forceinline__ void grid_reduce(double v[NP], const RedArgs& ra, uns
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // Thread t sums partials t, t + THREADS, ... in that order; RED_UNROLL loads are issued before
+  // they are added, so the tail is not a chain of dependent L2 round trips.
+  constexpr int RED_UNROLL = 8;
   double w[NP];
 #pragma unroll
   for (int k = 0; k < NP; ++k) w[k] = 0.0;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += THREADS) {
+  const unsigned G = gridDim.x;
+  for (unsigned b0 = threadIdx.x; b0 < G; b0 += THREADS * RED_UNROLL) {
+    double tmp[RED_UNROLL][NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) w[k] += __ldcg(ra.part + (size_t)b * NP + k);
+    for (int u = 0; u < RED_UNROLL; ++u) {
+      const unsigned b = b0 + u * THREADS;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) tmp[u][k] = b < G ? __ldcg(ra.part + (size_t)b * NP + k) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < RED_UNROLL; ++u)
+#pragma unroll
+      for (int k = 0; k < NP; ++k) w[k] += tmp[u][k];
   }
   block_sums<NP, THREADS>(w, sh);
   if (threadIdx.x == 0) {
