@@ -143,6 +143,28 @@ ok_solve_params ok_default_solve_params(double tol, int maxiter);
  * Needs OK_W_F64.  Synchronises `stream`.  |b| = 0 gives relres = |M x|. */
 int ok_true_residual(const ok_W* W, const void* b, const void* x, double* relres, void* stream);
 
+/* Allocation-free true residual.  The paper has no counterpart: this entry exists for callers that
+ * cannot let a library allocate device memory.  Two kinds of caller need it:
+ *   - programs that reserve (nearly) all of the GPU's memory for their own pool at start-up, where
+ *     a cudaMalloc issued here would fail or fragment that pool;
+ *   - latency-critical loops that cannot afford the device-wide synchronisation cudaMalloc and
+ *     cudaFree imply.
+ * It computes r = b - M x with the FP64 W (one fused application of M) and *relres = |r| / |b|
+ * (|M x| when b = 0), like ok_true_residual, but calls no cudaMalloc, cudaFree or allocating
+ * routine.
+ *   b, x: device [V][4][3] complex128, inputs.  r: device [V][4][3] complex128, output, supplied by
+ *   the caller, must not overlap b or x.  relres: host.
+ * Its reduction scratch is one fixed array of about 2 MiB in the library's device memory.  Every GPU
+ * that loads the library holds that array until the process exits.  The first call on a device
+ * looks up the array's address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls on a device share the array, so calls that overlap on
+ * the GPU (different streams or threads) race: serialise them.  Synchronises `stream`.
+ * Errors: OK_EINVAL for null or misaligned pointers, r overlapping an input, a handle without
+ * OK_W_F64, or a lattice of more than OK_STATIC_MAX_SITES sites; OK_ECUDA. */
+#define OK_STATIC_MAX_SITES (1 << 22)
+int ok_true_residual_static(const ok_W* W, const void* b, const void* x, void* r, double* relres,
+                            void* stream);
+
 /* Inspection: write the dense 12x12 forward matrix of one kind for every site, reconstructed from
  * the stored representation of precision `prec`: out = device [V][12][12] complex128 (row index
  * 3*spin + colour).  kind: 0 W^0; 1..4 W^+_mu (x, y, z, t); 5..7 W^{++}_ii (x, y, z);

@@ -22,7 +22,7 @@ from .build import LIB, build as build_library
 __all__ = [
     "load", "precompute_W", "apply_M", "bicgstab", "true_residual", "W_expand", "launch_count",
     "strerror", "OKError", "WHandle", "F64", "F32", "W_F64", "W_F32", "SOLVE_AUTO", "SOLVE_F64",
-    "SOLVE_MIXED", "header_functions", "trace_enable", "trace_read", "trace_reset",
+    "SOLVE_MIXED", "header_functions", "trace_enable", "trace_read", "trace_reset", "true_residual_static",
 ]
 
 F64, F32 = 0, 1
@@ -88,6 +88,7 @@ def load(path: str | None = None):
         "ok_bicgstab_ex": (i, [vp, vp, vp, ctypes.POINTER(ok_solve_params), ctypes.POINTER(ok_solve_info), vp]),
         "ok_default_solve_params": (ok_solve_params, [d, i]),
         "ok_true_residual": (i, [vp, vp, vp, ctypes.POINTER(d), vp]),
+        "ok_true_residual_static": (i, [vp, vp, vp, vp, ctypes.POINTER(d), vp]),
         "ok_W_expand": (i, [vp, i, i, vp, vp]),
         "ok_launch_count": (ctypes.c_ulonglong, []),
         "ok_trace_enable": (None, [i]),
@@ -281,6 +282,25 @@ def true_residual(W: WHandle, b, x, stream=None) -> float:
                                  ctypes.byref(r), _stream(stream))
     _check(st, "ok_true_residual")
     return float(r.value)
+
+
+def true_residual_static(W: WHandle, b, x, r=None, stream=None):
+    """ok_true_residual_static: r = b - M x into `r` (allocated here if not given) and |r| / |b|,
+    with the library's fixed scratch array instead of device allocations inside the call.
+    Returns (r, relres)."""
+    import torch
+    for t, n in ((b, "b"), (x, "x")):
+        _field_check(W, t, n)
+        if t.dtype != torch.complex128:
+            raise ValueError(f"{n} must be complex128")
+    if r is None:
+        r = torch.empty_like(b)
+    _field_check(W, r, "r")
+    rel = ctypes.c_double(0.0)
+    st = load().ok_true_residual_static(W.ptr, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                        ctypes.c_void_p(r.data_ptr()), ctypes.byref(rel), _stream(stream))
+    _check(st, "ok_true_residual_static")
+    return r, float(rel.value)
 
 
 def W_expand(W: WHandle, kind: int, prec=F64, stream=None):
