@@ -843,9 +843,14 @@ constexpr int SPLIT_SITES = 32;
 #ifndef OK_SPLIT_MINB
 #define OK_SPLIT_MINB 4
 #endif
+// Resident blocks for the variants with a fused reduction (they hold a few more live values).
+#ifndef OK_SPLIT_MINB_EPI
+#define OK_SPLIT_MINB_EPI 4
+#endif
+template <int EPI> constexpr int split_minb() { return EPI == EPI_NONE ? OK_SPLIT_MINB : OK_SPLIT_MINB_EPI; }
 
 template <typename R, int EPI>
-__global__ void __launch_bounds__(SPLIT_THREADS, OK_SPLIT_MINB) apply_split_kernel(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi,
+__global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB : OK_SPLIT_MINB_EPI) apply_split_kernel(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi,
                                                                                    cx<R>* __restrict__ out, Geom g, R c0q, R a_ii, R b_ii,
                                                                                    EpiArgs<R> ep) {
   if (EPI != EPI_NONE && ep.halt && *ep.halt) return;
@@ -854,12 +859,15 @@ __global__ void __launch_bounds__(SPLIT_THREADS, OK_SPLIT_MINB) apply_split_kern
   // buffer k & 1 for tile k only after the barrier of tile k - 1, which the forward half passes
   // only after it has read buffer (k - 2) & 1 = k & 1.
   __shared__ cx<R> xch[2][64][6];
+  __shared__ cx<R> xev[EPI == EPI_NONE ? 1 : 2][64][6];
   const int half = threadIdx.x >> 6;  // warp-uniform: 0 forward, 1 backward
   const int t = threadIdx.x & 63;
   Pair pr;
   pr.p = t & 1;
   pr.mask = 3u << (threadIdx.x & 30);
-  double red[3] = {0.0, 0.0, 0.0};
+  // Per-thread partial sums over this thread's few sites stay in the field's precision (fewer
+  // registers); the block and grid reductions that follow are FP64.
+  R red[3] = {0, 0, 0};
   const int ntiles = (g.V + SPLIT_SITES - 1) / SPLIT_SITES;
   int kb = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, kb ^= 1) {
@@ -926,6 +934,16 @@ __global__ void __launch_bounds__(SPLIT_THREADS, OK_SPLIT_MINB) apply_split_kern
       for (int q = 0; q < 2; ++q)
 #pragma unroll
         for (int k = 0; k < 3; ++k) xch[kb][t][3 * q + k] = acc.v[q][k];
+      // The epilogue's own half-spinor (rhat, psi or b at this site) is fetched here, on the
+      // backward warps, which would otherwise wait at the barrier for the longer forward half.
+      if (EPI != EPI_NONE) {
+        H6<R> ev;
+        load_half<R>(EPI == EPI_DOT ? ep.rhat : EPI == EPI_RESID ? ep.b : psi, s, pr.p, ev);
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) xev[kb][t][3 * q + k] = ev.v[q][k];
+      }
     }
   }
   __syncthreads();
@@ -935,14 +953,16 @@ __global__ void __launch_bounds__(SPLIT_THREADS, OK_SPLIT_MINB) apply_split_kern
 #pragma unroll
       for (int k = 0; k < 3; ++k) acc.v[q][k] = acc.v[q][k] + xch[kb][t][3 * q + k];
     // out_u = acc+ + acc- (p = 0 writes it), out_l = acc+ - acc- (p = 1)
-    H6<R> ap = partner(acc, pr.mask), o;
+    H6<R> ap = partner(acc, pr.mask), o, ev;
 #pragma unroll
     for (int q = 0; q < 2; ++q)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) o.v[q][k] = pr.p ? ap.v[q][k] - acc.v[q][k] : acc.v[q][k] + ap.v[q][k];
+      for (int k = 0; k < 3; ++k) {
+        o.v[q][k] = pr.p ? ap.v[q][k] - acc.v[q][k] : acc.v[q][k] + ap.v[q][k];
+        if (EPI != EPI_NONE) ev.v[q][k] = xev[kb][t][3 * q + k];
+      }
     if (EPI == EPI_RESID) {
-      H6<R> bv;
-      load_half<R>(ep.b, s, pr.p, bv);
+      const H6<R>& bv = ev;
 #pragma unroll
       for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -954,8 +974,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, OK_SPLIT_MINB) apply_split_kern
     }
     store_half<R>(out, s, pr.p, o);
     if (EPI == EPI_DOT) {
-      H6<R> rh;
-      load_half<R>(ep.rhat, s, pr.p, rh);
+      const H6<R>& rh = ev;
       cx<R> d = mk<R>(0, 0);
 #pragma unroll
       for (int q = 0; q < 2; ++q)
@@ -964,8 +983,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, OK_SPLIT_MINB) apply_split_kern
       red[0] += d.re;
       red[1] += d.im;
     } else if (EPI == EPI_TS) {
-      H6<R> x0;
-      load_half<R>(psi, s, pr.p, x0);
+      const H6<R>& x0 = ev;
       cx<R> d = mk<R>(0, 0);
       R n2 = 0;
 #pragma unroll
@@ -982,10 +1000,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS, OK_SPLIT_MINB) apply_split_kern
   }
   }  // tiles
   if (EPI == EPI_DOT || EPI == EPI_RESID) {
-    double v2[2] = {red[0], red[1]};
+    double v2[2] = {(double)red[0], (double)red[1]};
     grid_reduce<2, SPLIT_THREADS>(v2, ep.ra, ep.ticket);
   } else if (EPI == EPI_TS) {
-    grid_reduce<3, SPLIT_THREADS>(red, ep.ra, ep.ticket);
+    double v3[3] = {(double)red[0], (double)red[1], (double)red[2]};
+    grid_reduce<3, SPLIT_THREADS>(v3, ep.ra, ep.ticket);
   }
 }
 
@@ -1008,7 +1027,7 @@ static void launch_variant(const cx<R>* W, const cx<R>* psi, cx<R>* out, const G
   constexpr int v = apply_variant<R>();
   if constexpr (v == 2) {
     const int tiles = grid_for(g.V, SPLIT_SITES);
-    const int resident = sm_count() * OK_SPLIT_MINB;
+    const int resident = sm_count() * split_minb<EPI>();
     apply_split_kernel<R, EPI><<<tiles < resident ? tiles : resident, SPLIT_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep);
   }
   else if constexpr (v == 1)
