@@ -191,7 +191,7 @@ def apply_source_hash():
 
 def ncu_traffic(kernel_key):
     """DRAM bytes per launch recorded by the committed ncu summary, if it still matches the source."""
-    path = os.path.join(ROOT, "profiles", "apply_f32_16x16x16x32.md")
+    path = os.path.join(ROOT, "profiles", "apply_f32_split_16x16x16x32.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
