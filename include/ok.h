@@ -52,9 +52,14 @@ typedef struct {
 
 typedef enum { OK_F64 = 0, OK_F32 = 1 } ok_prec;
 
-/* Which stored precisions a W handle carries (bit mask for ok_precompute_W). */
+/* Which stored copies a W handle carries (bit mask for ok_precompute_W).  OK_W_DF64 keeps FP64
+ * accuracy as double-float pairs (hi + lo, two floats, about 48 significand bits): FP64 applications
+ * and residuals on such a handle run on the FP32 pipes, which GB300 executes 58 times faster than its
+ * FP64 pipe, with errors of about 1e-14 relative.  When a handle has both OK_W_F64 and OK_W_DF64,
+ * FP64 work uses the native OK_W_F64 copy. */
 #define OK_W_F64 1
 #define OK_W_F32 2
+#define OK_W_DF64 4
 
 /* Coefficients of the tree-level, tadpole-improved OK action (Sec. 1; they enter the W formulas,
  * Eqs. shifted_W_first .. shifted_W_last).  u0 <= 0: u0 is computed from the mean plaquette of

@@ -21,12 +21,12 @@ from .build import LIB, build as build_library
 
 __all__ = [
     "load", "precompute_W", "apply_M", "bicgstab", "true_residual", "W_expand", "launch_count",
-    "strerror", "OKError", "WHandle", "F64", "F32", "W_F64", "W_F32", "SOLVE_AUTO", "SOLVE_F64",
+    "strerror", "OKError", "WHandle", "F64", "F32", "W_F64", "W_F32", "W_DF64", "SOLVE_AUTO", "SOLVE_F64",
     "SOLVE_MIXED", "header_functions", "trace_enable", "trace_read", "trace_reset", "true_residual_static",
 ]
 
 F64, F32 = 0, 1
-W_F64, W_F32 = 1, 2
+W_F64, W_F32, W_DF64 = 1, 2, 4
 SOLVE_AUTO, SOLVE_F64, SOLVE_MIXED = 0, 1, 2
 OK_ENOCONV, OK_EBREAKDOWN = -4, -5
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ok.h")

@@ -15,6 +15,8 @@
 // BiCGStab reductions (ok_reduce.cuh) without a second pass over the output.
 #include "ok_launch.cuh"
 
+#include <type_traits>
+
 namespace okgb {
 
 constexpr int APPLY_THREADS = 128;
@@ -63,12 +65,74 @@ __device__ __forceinline__ void store_spinor<float>(cx<float>* __restrict__ out,
   for (int k = 0; k < 6; ++k) p[k] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
 }
 
+// Double-float fields: input spinors are (re.hi, re.lo, im.hi, im.lo) per complex number; the
+// kernel's outputs are written as FP64 complex numbers (hi + lo rounded to double).
+template <>
+__device__ __forceinline__ void load_spinor<dd>(const cx<dd>* __restrict__ psi, int site, cx<dd> (&v)[12]) {
+  const float4* p = reinterpret_cast<const float4*>(psi) + (size_t)site * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    float4 d = __ldg(p + k);
+    v[k] = mk(dd(d.x, d.y), dd(d.z, d.w));
+  }
+}
+
+template <>
+__device__ __forceinline__ void store_spinor<dd>(cx<dd>* __restrict__ out, int site, const cx<dd> (&v)[12]) {
+  double2* p = reinterpret_cast<double2*>(out) + (size_t)site * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) p[k] = make_double2((double)v[k].re, (double)v[k].im);
+}
+
+// Right-hand side of the residual epilogue: FP64 for the double-float kernel, the field's own
+// precision otherwise.
+template <typename R>
+__device__ __forceinline__ void load_rhs(const cx<R>* __restrict__ b, int site, cx<R> (&v)[12]) {
+  if constexpr (std::is_same<R, dd>::value) {
+    const double2* p = reinterpret_cast<const double2*>(b) + (size_t)site * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 d = __ldg(p + k);
+      v[k] = mk(R(d.x), R(d.y));
+    }
+  } else {
+    load_spinor<R>(b, site, v);
+  }
+}
+
+// Read-only load of one FP32 W element.  Variant 0: plain __ldg; 1: not allocated in L1 (a W
+// element is used by exactly one thread, so L1 is left to the neighbour spinors); 2: with a 256-byte
+// L2 prefetch hint (a matrix element row of 32 sites is 256 bytes, read by two warps); 3: both.
+#ifndef OK_W_LOAD
+#define OK_W_LOAD 0
+#endif
+__device__ __forceinline__ float2 ldg_w(const float2* p) {
+  float2 d;
+#if OK_W_LOAD == 1
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(d.x), "=f"(d.y) : "l"(p));
+#elif OK_W_LOAD == 2
+  asm volatile("ld.global.nc.L2::256B.v2.f32 {%0, %1}, [%2];" : "=f"(d.x), "=f"(d.y) : "l"(p));
+#elif OK_W_LOAD == 3
+  asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v2.f32 {%0, %1}, [%2];" : "=f"(d.x), "=f"(d.y) : "l"(p));
+#else
+  d = __ldg(p);
+#endif
+  return d;
+}
+
 // Matrix m of the site record of `site`.
 template <typename R>
 __device__ __forceinline__ M3<R> wmat(const cx<R>* __restrict__ W, int site, int m) {
   const size_t base = ((size_t)(site >> 5) * NMAT + m) * (9 * LANES) + (site & 31);
   M3<R> a;
-  if constexpr (sizeof(R) == 8) {
+  if constexpr (std::is_same<R, dd>::value) {
+    const float4* p = reinterpret_cast<const float4*>(W) + base;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      float4 d = __ldg(p + e * LANES);
+      a.e[e] = mk<R>(dd(d.x, d.y), dd(d.z, d.w));
+    }
+  } else if constexpr (std::is_same<R, double>::value) {
     const double2* p = reinterpret_cast<const double2*>(W) + base;
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
@@ -79,7 +143,7 @@ __device__ __forceinline__ M3<R> wmat(const cx<R>* __restrict__ W, int site, int
     const float2* p = reinterpret_cast<const float2*>(W) + base;
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
-      float2 d = __ldg(p + e * LANES);
+      float2 d = ldg_w(p + e * LANES);
       a.e[e] = mk<R>(d.x, d.y);
     }
   }
@@ -408,16 +472,18 @@ __global__ void __launch_bounds__(APPLY_THREADS) apply_kernel(const cx<R>* __res
       }
     if (EPI == EPI_RESID) {
       cx<R> bv[12];
-      load_spinor<R>(ep.b, s, bv);
+      load_rhs<R>(ep.b, s, bv);
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         o[k] = bv[k] - o[k];
-        red[0] += (double)o[k].re * o[k].re + (double)o[k].im * o[k].im;
-        red[1] += (double)bv[k].re * bv[k].re + (double)bv[k].im * bv[k].im;
+        const double ore = (double)o[k].re, oim = (double)o[k].im;
+        const double bre = (double)bv[k].re, bim = (double)bv[k].im;
+        red[0] += ore * ore + oim * oim;
+        red[1] += bre * bre + bim * bim;
       }
     }
     store_spinor<R>(out, s, o);
-    if (EPI == EPI_DOT) {
+    if constexpr (EPI == EPI_DOT) {
       cx<R> rh[12];
       load_spinor<R>(ep.rhat, s, rh);
       cx<R> d = mk<R>(0, 0);
@@ -425,7 +491,7 @@ __global__ void __launch_bounds__(APPLY_THREADS) apply_kernel(const cx<R>* __res
       for (int k = 0; k < 12; ++k) d = fma_cj(rh[k], o[k], d);
       red[0] = d.re;
       red[1] = d.im;
-    } else if (EPI == EPI_TS) {
+    } else if constexpr (EPI == EPI_TS) {
       cx<R> d = mk<R>(0, 0);
       R n2 = 0;
 #pragma unroll
@@ -1060,6 +1126,26 @@ int launch_apply(const ok_W* Wh, const cx<R>* psi, cx<R>* out, int epi, const Ep
 
 // Upper bound of the grid size of any apply variant (sizes the reduction partials).
 int apply_blocks_needed(const ok_W* Wh) { return grid_for(Wh->g.V, SPLIT_SITES); }
+
+// FP64-accurate application with the double-float copy of W: psi in double-float, out in FP64;
+// EPI_NONE or EPI_RESID (b in FP64).  One thread per site, as for native FP64.
+int launch_apply_df(const ok_W* Wh, const cx<dd>* psi_df, cx<double>* out, int epi, const EpiArgs<dd>& ep, cudaStream_t st) {
+  const cx<dd>* W = (const cx<dd>*)Wh->Wdf;
+  if (!W || (epi != EPI_NONE && epi != EPI_RESID)) return OK_EINVAL;
+  const Geom& g = Wh->g;
+  const dd c0q(Wh->sc.c0q), a(Wh->sc.a_ii), b(Wh->sc.b_ii);
+  const int nb = grid_for(g.V, APPLY_THREADS);
+  cx<dd>* o = reinterpret_cast<cx<dd>*>(out);  // the double-float kernel stores FP64 outputs
+  {
+    TraceScope ts(epi == EPI_RESID ? "apply_df64_resid" : "apply_df64", st);
+    if (epi == EPI_RESID)
+      apply_kernel<dd, EPI_RESID><<<nb, APPLY_THREADS, 0, st>>>(W, psi_df, o, g, c0q, a, b, ep);
+    else
+      apply_kernel<dd, EPI_NONE><<<nb, APPLY_THREADS, 0, st>>>(W, psi_df, o, g, c0q, a, b, ep);
+  }
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
 
 template int launch_apply<double>(const ok_W*, const cx<double>*, cx<double>*, int, const EpiArgs<double>&, cudaStream_t);
 template int launch_apply<float>(const ok_W*, const cx<float>*, cx<float>*, int, const EpiArgs<float>&, cudaStream_t);

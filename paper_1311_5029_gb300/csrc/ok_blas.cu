@@ -179,6 +179,16 @@ __global__ void __launch_bounds__(BLAS_THREADS) norms_kernel(const double2* __re
   grid_reduce<2, BLAS_THREADS>(red, ra, &st->ticket[6]);
 }
 
+// FP64 -> double-float: each double d becomes (hi, lo) = (float(d), float(d - hi)).
+__global__ void __launch_bounds__(BLAS_THREADS) to_df_kernel(const double2* __restrict__ in, float4* __restrict__ out,
+                                                             long long n) {
+  OK_GRID_STRIDE(i, n) {
+    const double2 v = in[i];
+    const dd re(v.x), im(v.y);
+    out[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+}
+
 // ---------------------------------------------------------------------------- launchers
 static int g_sms = 0;
 
@@ -275,6 +285,15 @@ int launch_accum_x(cx<double>* x64, cx<float>* x32, long long n, cudaStream_t st
   {
     TraceScope ts("accum_x", strm);
     accum_x_kernel<<<blas_blocks(n), BLAS_THREADS, 0, strm>>>((double2*)x64, (float2*)x32, n);
+  }
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+int launch_to_df(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t strm) {
+  {
+    TraceScope ts("to_df64", strm);
+    to_df_kernel<<<blas_blocks(n), BLAS_THREADS, 0, strm>>>((const double2*)in, (float4*)out, n);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;

@@ -85,6 +85,7 @@ void ok_free_W(ok_W* W) {
   if (!W) return;
   if (W->W64) cudaFree(W->W64);
   if (W->W32) cudaFree(W->W32);
+  if (W->Wdf) cudaFree(W->Wdf);
   delete W;
 }
 
@@ -110,9 +111,23 @@ int ok_apply_M(const ok_W* W, ok_prec prec, const void* psi, void* out, void* st
   if (a < b + bytes && b < a + bytes) return OK_EINVAL;  // overlapping ranges
   if (((uintptr_t)psi | (uintptr_t)out) & 15) return OK_EINVAL;
   if (prec == OK_F64) {
-    if (!W->W64) return OK_EINVAL;
-    EpiArgs<double> e{};
-    return launch_apply<double>(W, (const cx<double>*)psi, (cx<double>*)out, EPI_NONE, e, (cudaStream_t)stream);
+    if (W->W64) {
+      EpiArgs<double> e{};
+      return launch_apply<double>(W, (const cx<double>*)psi, (cx<double>*)out, EPI_NONE, e, (cudaStream_t)stream);
+    }
+    if (!W->Wdf) return OK_EINVAL;
+    // double-float copy: convert psi into stream-ordered scratch, apply, release the scratch
+    cudaStream_t st = (cudaStream_t)stream;
+    void* psi_df = nullptr;
+    OK_CUDA_TRY(cudaMallocAsync(&psi_df, bytes, st));
+    int rc = launch_to_df((const cx<double>*)psi, (cx<dd>*)psi_df, 12LL * W->g.V, st);
+    if (rc == OK_SUCCESS) {
+      EpiArgs<dd> e{};
+      rc = launch_apply_df(W, (const cx<dd>*)psi_df, (cx<double>*)out, EPI_NONE, e, st);
+    }
+    cudaError_t fe = cudaFreeAsync(psi_df, st);
+    if (rc == OK_SUCCESS && fe != cudaSuccess) { set_cuda_error(fe); rc = OK_ECUDA; }
+    return rc;
   }
   if (!W->W32) return OK_EINVAL;
   EpiArgs<float> e{};

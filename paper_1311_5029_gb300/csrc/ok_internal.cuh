@@ -10,6 +10,61 @@
 
 namespace okgb {
 
+// ---------------------------------------------------------------------------- double-float
+// A real number held as the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi) / 2
+// (about 48 significand bits).  Arithmetic uses the error-free transformations TwoSum (Knuth) and
+// TwoProd (with FMA), as in Joldes, Muller and Popescu, "Tight and rigorous error bounds for basic
+// building blocks of double-word arithmetic", ACM TOMS 44 (2017): the products are the "DWTimesDW"
+// form and the sums add the low parts without a second TwoSum, so an operation's absolute error is
+// a few 2^-48 times the magnitude of its operands.  On GB300 the FP32 pipes are 58 times faster
+// than the FP64 pipe, which makes this the faster way to FP64-level accuracy for the stencil.
+// nvcc does not reassociate floating-point expressions, and none of the sums below contains a
+// product that FMA contraction could merge.
+struct dd {
+  float hi, lo;
+  dd() = default;
+  __host__ __device__ __forceinline__ constexpr dd(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ __forceinline__ dd(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ __forceinline__ dd(int i) : dd((double)i) {}
+  __host__ __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__host__ __device__ __forceinline__ dd dd_renorm(float s, float e) {
+  const float h = s + e;
+  return dd(h, e - (h - s));
+}
+__host__ __device__ __forceinline__ dd operator+(dd a, dd b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  return dd_renorm(s, e);
+}
+__host__ __device__ __forceinline__ dd operator-(dd a) { return dd(-a.hi, -a.lo); }
+__host__ __device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
+__host__ __device__ __forceinline__ dd operator*(dd a, dd b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return dd_renorm(p, e);
+}
+// fma overloads in this namespace so that templates calling fma(x, y, z) work for float, double
+// and dd alike.
+__host__ __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+__host__ __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+__host__ __device__ __forceinline__ dd fma(dd a, dd b, dd c) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float s = p + c.hi;
+  const float bb = s - p;
+  float t = (p - (s - bb)) + (c.hi - bb);
+  t += e + c.lo;
+  return dd_renorm(s, t);
+}
+
 // ---------------------------------------------------------------------------- complex numbers
 template <typename R> struct cx { R re, im; };
 
@@ -124,6 +179,7 @@ struct ok_W {
   okgb::WScalars sc;
   void* W64;     // cx<double>[nblk * SITE_ELEMS * 32]
   void* W32;     // cx<float>[...]
+  void* Wdf;     // cx<dd>[...]: FP64-accurate double-float copy
   size_t bytes;
   int device;
 };

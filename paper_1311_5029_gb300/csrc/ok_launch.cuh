@@ -24,6 +24,10 @@ template <typename R> struct EpiArgs {
 template <typename R>
 int launch_apply(const ok_W* W, const cx<R>* psi, cx<R>* out, int epi, const EpiArgs<R>& ep, cudaStream_t st);
 int apply_blocks_needed(const ok_W* W);
+// FP64-accurate apply with the double-float W copy (psi double-float, out FP64; EPI_NONE/EPI_RESID).
+int launch_apply_df(const ok_W* W, const cx<dd>* psi_df, cx<double>* out, int epi, const EpiArgs<dd>& ep, cudaStream_t st);
+// FP64 complex -> double-float complex (n complex numbers).
+int launch_to_df(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t st);
 
 int blas_blocks(long long units);
 int sm_count();  // multiprocessors of the current device (cached)

@@ -178,6 +178,7 @@ __global__ void scalars_kernel(const double* __restrict__ plaq_part, int nparts,
 struct WOut {
   cx<double>* W64;
   cx<float>* W32;
+  cx<dd>* Wdf;
 };
 
 __device__ __forceinline__ void store_mat(const WOut& o, int site, int m, const M3<double>& a) {
@@ -188,6 +189,7 @@ __device__ __forceinline__ void store_mat(const WOut& o, int site, int m, const 
   for (int e = 0; e < 9; ++e) {
     if (o.W64) o.W64[base + (size_t)e * LANES] = a.e[e];
     if (o.W32) o.W32[base + (size_t)e * LANES] = mk<float>((float)a.e[e].re, (float)a.e[e].im);
+    if (o.Wdf) o.Wdf[base + (size_t)e * LANES] = mk<dd>(dd(a.e[e].re), dd(a.e[e].im));
   }
 }
 
@@ -491,7 +493,7 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
     scalars_kernel<<<1, 256, 0, st>>>(part, nb1, g, *c, dsc);
   }
   OK_LAUNCH_CHECK();
-  WOut o{(cx<double>*)W->W64, (cx<float>*)W->W32};
+  WOut o{(cx<double>*)W->W64, (cx<float>*)W->W32, (cx<dd>*)W->Wdf};
   int nb2 = grid_for(g.V, K2_THREADS);
   for (int part_id = 0; part_id < 5; ++part_id) {
     {
@@ -507,7 +509,7 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
                int precs, cudaStream_t st, ok_W** W_out) {
   if (!lat || !links || !c || !W_out) return OK_EINVAL;
   if (links_prec != OK_F64 && links_prec != OK_F32) return OK_EINVAL;
-  if (precs <= 0 || (precs & ~(OK_W_F64 | OK_W_F32))) return OK_EINVAL;
+  if (precs <= 0 || (precs & ~(OK_W_F64 | OK_W_F32 | OK_W_DF64))) return OK_EINVAL;
   if (!(c->u0 > 0.0) && c->u0 > 0.0) return OK_EINVAL;
   *W_out = nullptr;
   Geom g;
@@ -529,6 +531,7 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
     if (dsc) cudaFree(dsc);
     if (W->W64) cudaFree(W->W64);
     if (W->W32) cudaFree(W->W32);
+    if (W->Wdf) cudaFree(W->Wdf);
     delete W;
     return code;
   };
@@ -545,7 +548,14 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
     e = cudaMemsetAsync(W->W32, 0, elems * sizeof(cx<float>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
   }
-  W->bytes = (W->W64 ? elems * sizeof(cx<double>) : 0) + (W->W32 ? elems * sizeof(cx<float>) : 0);
+  if (precs & OK_W_DF64) {
+    e = cudaMalloc(&W->Wdf, elems * sizeof(cx<dd>));
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
+    e = cudaMemsetAsync(W->Wdf, 0, elems * sizeof(cx<dd>), st);
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
+  }
+  W->bytes = (W->W64 ? elems * sizeof(cx<double>) : 0) + (W->W32 ? elems * sizeof(cx<float>) : 0) +
+             (W->Wdf ? elems * sizeof(cx<dd>) : 0);
   int nb1 = grid_for(g.V, K1_THREADS);
   e = cudaMalloc(&EB, (size_t)g.V * 6 * 9 * sizeof(cx<double>));
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
@@ -570,7 +580,7 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
 
 int expand(const ok_W* W, ok_prec prec, int kind, void* out, cudaStream_t st) {
   if (!W || !out || kind < 0 || kind > 13) return OK_EINVAL;
-  const void* src = prec == OK_F64 ? W->W64 : prec == OK_F32 ? W->W32 : nullptr;
+  const void* src = prec == OK_F64 ? (W->W64 ? W->W64 : W->Wdf) : prec == OK_F32 ? W->W32 : nullptr;
   if (!src) return OK_EINVAL;
   WScalars* dsc = nullptr;
   OK_CUDA_TRY(cudaMallocAsync((void**)&dsc, sizeof(WScalars), st));
@@ -578,7 +588,9 @@ int expand(const ok_W* W, ok_prec prec, int kind, void* out, cudaStream_t st) {
   if (e != cudaSuccess) { cudaFreeAsync(dsc, st); set_cuda_error(e); return OK_ECUDA; }
   int nb = grid_for(W->g.V, 64);
   TraceScope ts("expand", st);
-  if (prec == OK_F64)
+  if (prec == OK_F64 && !W->W64)
+    expand_kernel<dd><<<nb, 64, 0, st>>>((const cx<dd>*)src, W->g, dsc, kind, (cx<double>*)out);
+  else if (prec == OK_F64)
     expand_kernel<double><<<nb, 64, 0, st>>>((const cx<double>*)src, W->g, dsc, kind, (cx<double>*)out);
   else
     expand_kernel<float><<<nb, 64, 0, st>>>((const cx<float>*)src, W->g, dsc, kind, (cx<double>*)out);

@@ -86,11 +86,20 @@ int iterate(const ok_W* W, const IterBufs<R>& b, long long n, SolverState* dst, 
   return OK_SUCCESS;
 }
 
-// out = b - M x in FP64 with |out|^2 in state aux[0] and |b|^2 in state bb (and aux[1]).
+// out = b - M x in FP64 with |out|^2 in state aux[0] and |b|^2 in state bb (and aux[1]).  With the
+// native FP64 W copy when the handle has one, else with the double-float copy (x converted first
+// into `xdf`, n complex double-floats of scratch).
 int residual64(const ok_W* W, const cx<double>* bvec, const cx<double>* x, cx<double>* out, SolverState* dst, double* part,
-               cudaStream_t st) {
-  EpiArgs<double> e{nullptr, bvec, RedArgs{dst, part, nullptr, FIN_RESID}, &dst->ticket[5], nullptr};
-  return launch_apply<double>(W, x, out, EPI_RESID, e, st);
+               cx<dd>* xdf, cudaStream_t st) {
+  if (W->W64) {
+    EpiArgs<double> e{nullptr, bvec, RedArgs{dst, part, nullptr, FIN_RESID}, &dst->ticket[5], nullptr};
+    return launch_apply<double>(W, x, out, EPI_RESID, e, st);
+  }
+  if (!W->Wdf || !xdf) return OK_EINVAL;
+  OK_TRY(launch_to_df(x, xdf, 12LL * W->g.V, st));
+  EpiArgs<dd> e{nullptr, reinterpret_cast<const cx<dd>*>(bvec), RedArgs{dst, part, nullptr, FIN_RESID}, &dst->ticket[5],
+                nullptr};
+  return launch_apply_df(W, xdf, out, EPI_RESID, e, st);
 }
 
 }  // namespace
@@ -101,9 +110,11 @@ int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solv
   if (!W || !bvec || !x || !prm) return OK_EINVAL;
   if (!(prm->tol > 0.0) || prm->maxiter < 1 || prm->max_restarts < 0 || prm->check_every < 1) return OK_EINVAL;
   int mode = prm->mode;
-  if (mode == OK_SOLVE_AUTO) mode = (W->W32 && W->W64) ? OK_SOLVE_MIXED : OK_SOLVE_F64;
+  const bool has64 = W->W64 || W->Wdf;  // an FP64-accurate copy for the true residual
+  if (mode == OK_SOLVE_AUTO) mode = (W->W32 && has64) ? OK_SOLVE_MIXED : OK_SOLVE_F64;
   if (mode != OK_SOLVE_F64 && mode != OK_SOLVE_MIXED) return OK_EINVAL;
-  if (!W->W64) return OK_EINVAL;
+  if (mode == OK_SOLVE_F64 && !W->W64) return OK_EINVAL;  // the plain FP64 iteration uses native FP64
+  if (!has64) return OK_EINVAL;
   if (mode == OK_SOLVE_MIXED && (!W->W32 || !(prm->delta > 0.0 && prm->delta < 1.0))) return OK_EINVAL;
   if ((const void*)bvec == (const void*)x) return OK_EINVAL;
 
@@ -131,6 +142,11 @@ int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solv
   IterBufs<float> b32{};
   cx<double>* r64 = ws.get<cx<double>>(n, &err);
   if (!r64) { set_cuda_error(err); return OK_ENOMEM; }
+  cx<dd>* xdf = nullptr;
+  if (!W->W64) {
+    xdf = ws.get<cx<dd>>(n, &err);
+    if (!xdf) { set_cuda_error(err); return OK_ENOMEM; }
+  }
   if (mode == OK_SOLVE_F64) {
     b64.x = x; b64.r = r64;
     b64.rhat = ws.get<cx<double>>(n, &err); b64.p = ws.get<cx<double>>(n, &err); b64.v = ws.get<cx<double>>(n, &err);
@@ -161,7 +177,7 @@ int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solv
     OK_CUDA_TRY(cudaMemcpyAsync(r64, bvec, n * sizeof(cx<double>), cudaMemcpyDeviceToDevice, st));
     h->aux[0] = h->bb;
   } else {
-    OK_TRY(residual64(W, bvec, x, r64, dst, part, st));
+    OK_TRY(residual64(W, bvec, x, r64, dst, part, xdf, st));
     inf.fp64_applies++;
   }
   if (mode == OK_SOLVE_F64) OK_TRY(launch_restart<double>(r64, b64.rhat, b64.p, n, dst, part, st));
@@ -187,7 +203,7 @@ int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solv
     if (halt == HALT_NONFINITE) return finish(OK_ENONFINITE, rr_true);
     // true residual
     if (mode == OK_SOLVE_MIXED) OK_TRY(launch_accum_x(x, b32.x, n, st));
-    OK_TRY(residual64(W, bvec, x, r64, dst, part, st));
+    OK_TRY(residual64(W, bvec, x, r64, dst, part, xdf, st));
     inf.fp64_applies++;
     OK_TRY(read_state(dst, h, st));
     rr_true = h->aux[0];
@@ -212,7 +228,7 @@ int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solv
 }
 
 int true_residual(const ok_W* W, const cx<double>* bvec, const cx<double>* x, double* relres, cudaStream_t st) {
-  if (!W || !bvec || !x || !relres || !W->W64) return OK_EINVAL;
+  if (!W || !bvec || !x || !relres || !(W->W64 || W->Wdf)) return OK_EINVAL;
   const long long n = 12LL * W->g.V;
   Workspace ws;
   ws.st = st;
@@ -220,10 +236,11 @@ int true_residual(const ok_W* W, const cx<double>* bvec, const cx<double>* x, do
   double* part = ws.get<double>((size_t)apply_blocks_needed(W) * 4, &err);
   SolverState* dst = ws.get<SolverState>(1, &err);
   cx<double>* r = ws.get<cx<double>>(n, &err);
+  cx<dd>* xdf = W->W64 ? nullptr : ws.get<cx<dd>>(n, &err);
   HostState hs;
-  if (!part || !dst || !r || !hs.h) { if (err != cudaSuccess) set_cuda_error(err); return OK_ENOMEM; }
+  if (!part || !dst || !r || !hs.h || (!W->W64 && !xdf)) { if (err != cudaSuccess) set_cuda_error(err); return OK_ENOMEM; }
   OK_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(SolverState), st));
-  OK_TRY(residual64(W, bvec, x, r, dst, part, st));
+  OK_TRY(residual64(W, bvec, x, r, dst, part, xdf, st));
   OK_TRY(read_state(dst, hs.h, st));
   double rr = hs.h->aux[0], bb = hs.h->aux[1];
   *relres = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);

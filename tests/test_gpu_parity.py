@@ -172,3 +172,45 @@ def test_argument_errors():
         ok.precompute_W(U, synth.placeholder_coeffs(1.0).replace(c3=float("nan")))
     with pytest.raises(ValueError):
         ok.apply_M(W32, psi32.reshape(-1)[:10])
+
+
+# ----------------------------------------------------------------------------- double-float FP64
+@pytest.mark.parametrize("case", SMALL_CASES[:5], ids=CASE_IDS[:5])
+def test_double_float_copy_matches_oracle(case):
+    """A handle holding only the double-float FP64 copy (OK_W_DF64): its stored W and its FP64
+    applications must meet the FP64 bar (1e-12) against the oracle."""
+    _, dims, bc, eps, c = case
+    U = synth.random_links(dims, eps, 5100 + sum(dims))
+    psi = synth.gaussian_source(dims, 5200 + sum(dims))
+    W = ok.precompute_W(to_dev(U), c, bc, ok.W_DF64)
+    ref = wform.forward_set(U, c)
+    V = int(np.prod(dims))
+    for kind, name in enumerate(ok.W_KINDS):
+        got = ok.W_expand(W, kind, ok.F64).cpu().numpy()
+        assert rel_max(got, ref[name].reshape(V, 12, 12)) < FP64_TOL, name
+    got = ok.apply_M(W, to_dev(psi)).cpu().numpy()
+    exp = wform.apply(U, c, psi, bc)
+    assert rel_l2(got, exp) < FP64_TOL
+    assert rel_max(got, exp) < 10 * FP64_TOL
+
+
+def test_double_float_true_residual_equals_native():
+    dims, bc = (6, 5, 4, 7), (1, 1, 1, -1)
+    U = to_dev(synth.random_links(dims, 0.4, 5301))
+    c = synth.random_coeffs(5302)
+    Wn = ok.precompute_W(U, c, bc, ok.W_F64)
+    Wd = ok.precompute_W(U, c, bc, ok.W_DF64)
+    b = to_dev(synth.gaussian_source(dims, 5303))
+    x = to_dev(synth.gaussian_source(dims, 5304)) * 0.2
+    rn, rd = ok.true_residual(Wn, b, x), ok.true_residual(Wd, b, x)
+    assert abs(rn - rd) < 1e-12 * rn
+
+
+def test_double_float_16cube32_sampled():
+    dims, U, c, src = synth.workload_inputs("16^3x32")
+    W = ok.precompute_W(to_dev(U), c, (1, 1, 1, 1), ok.W_DF64 | ok.W_F32)
+    V = int(np.prod(dims))
+    sites = _sample_sites(V)
+    exp = direct.apply_at(U, c, src, sites)
+    got = ok.apply_M(W, to_dev(src)).cpu().numpy().reshape(V, 4, 3)[sites]
+    assert rel_max(got, exp) < 10 * FP64_TOL

@@ -106,3 +106,15 @@ def test_solves_are_deterministic():
         xa, ia = ok.bicgstab(W, b, tol=TOL, mode=mode)
         xb, ib = ok.bicgstab(W, b, tol=TOL, mode=mode)
         assert torch.equal(xa, xb) and ia["iters"] == ib["iters"]
+
+
+def test_mixed_solve_with_double_float_residuals():
+    """FP32 iteration with reliable updates whose true residuals use the double-float FP64 copy."""
+    dims, U, c, b = synth.workload_inputs("16^3x32")
+    bc = (1, 1, 1, 1)
+    W = ok.precompute_W(to_dev(U), c, bc, ok.W_DF64 | ok.W_F32)
+    x, info = ok.bicgstab(W, to_dev(b), tol=TOL, mode=ok.SOLVE_MIXED, delta=1e-4)
+    assert info["status"] == 0 and info["true_relres"] < TOL
+    assert oracle_relres(U, c, b, x.cpu().numpy(), bc, lean=True) < TOL
+    with pytest.raises(ok.OKError):   # plain FP64 iteration needs the native copy
+        ok.bicgstab(W, to_dev(b), tol=TOL, mode=ok.SOLVE_F64)
