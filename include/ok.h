@@ -50,7 +50,9 @@ typedef struct {
 
 #define OK_MAX_SITES (1 << 27)
 
-typedef enum { OK_F64 = 0, OK_F32 = 1 } ok_prec;
+/* Precision of an application of M: OK_F64 (complex128 fields, FP64-accurate W), OK_F32 (complex64
+ * fields, FP32 W) or OK_F32_W16 (complex64 fields and FP32 arithmetic with the FP16 copy of W). */
+typedef enum { OK_F64 = 0, OK_F32 = 1, OK_F32_W16 = 2 } ok_prec;
 
 /* Which stored copies a W handle carries (bit mask for ok_precompute_W).  OK_W_DF64 keeps FP64
  * accuracy as double-float pairs (hi + lo, two floats, about 48 significand bits): FP64 applications
@@ -60,6 +62,7 @@ typedef enum { OK_F64 = 0, OK_F32 = 1 } ok_prec;
 #define OK_W_F64 1
 #define OK_W_F32 2
 #define OK_W_DF64 4
+#define OK_W_F16 8   /* half-precision copy (relative rounding 2^-11) for the low-precision iteration */
 
 /* Coefficients of the tree-level, tadpole-improved OK action (Sec. 1; they enter the W formulas,
  * Eqs. shifted_W_first .. shifted_W_last).  u0 <= 0: u0 is computed from the mean plaquette of
@@ -82,6 +85,7 @@ typedef struct {
 #define OK_SOLVE_AUTO   0  /* mixed if the handle has OK_W_F32 and OK_W_F64, else plain FP64 */
 #define OK_SOLVE_F64    1  /* plain FP64 BiCGStab (needs OK_W_F64) */
 #define OK_SOLVE_MIXED  2  /* FP32 BiCGStab with FP64 reliable updates (needs both precisions) */
+#define OK_SOLVE_MIXED16 3 /* as OK_SOLVE_MIXED with the FP16 W copy in the FP32 iteration (OK_W_F16) */
 
 typedef struct {
     double tol;          /* stop when |b - M x| / |b| < tol (true FP64 residual) */
@@ -124,7 +128,8 @@ int ok_W_info(const ok_W* W, ok_lattice* lat, int* W_precs, size_t* bytes);
 
 /* out = M psi (Eq. dslash with M in the form of Eq. minFlopForm: the on-site W^0, the 8 nearest,
  * 6 next-to-nearest straight and 12 diagonal neighbours), using the handle's stored matrices of
- * precision `prec`, arithmetic in that precision.
+ * precision `prec`, arithmetic in that precision (OK_F32_W16: complex64 fields, FP32 arithmetic,
+ * matrices read from the OK_W_F16 copy and widened to FP32).
  *   psi, out: device [V][4][3] complex in `prec`; out must not overlap psi.
  * Errors: OK_EINVAL (null, aliasing, handle lacks `prec`), OK_ECUDA.  Asynchronous. */
 int ok_apply_M(const ok_W* W, ok_prec prec, const void* psi, void* out, void* stream);
@@ -145,7 +150,7 @@ ok_solve_params ok_default_solve_params(double tol, int maxiter);
 
 /* True residual |b - M x| / |b| in FP64 (the check that judges every solve): one FP64
  * application of M fused with the norms.  b, x: device [V][4][3] complex128; relres: host.
- * Needs OK_W_F64.  Synchronises `stream`.  |b| = 0 gives relres = |M x|. */
+ * Needs OK_W_F64 or OK_W_DF64.  Synchronises `stream`.  |b| = 0 gives relres = |M x|. */
 int ok_true_residual(const ok_W* W, const void* b, const void* x, double* relres, void* stream);
 
 /* Allocation-free true residual.  The paper has no counterpart: this entry exists for callers that
@@ -171,7 +176,8 @@ int ok_true_residual_static(const ok_W* W, const void* b, const void* x, void* r
                             void* stream);
 
 /* Inspection: write the dense 12x12 forward matrix of one kind for every site, reconstructed from
- * the stored representation of precision `prec`: out = device [V][12][12] complex128 (row index
+ * the stored representation of precision `prec` (OK_F32_W16: the half-precision copy; OK_F64 reads
+ * OK_W_F64, else OK_W_DF64): out = device [V][12][12] complex128 (row index
  * 3*spin + colour).  kind: 0 W^0; 1..4 W^+_mu (x, y, z, t); 5..7 W^{++}_ii (x, y, z);
  * 8..10 W^{++}_ij (xy, xz, yz); 11..13 W^{+-}_ij (xy, xz, yz; they multiply psi_{x+i-j}). */
 int ok_W_expand(const ok_W* W, ok_prec prec, int kind, void* out, void* stream);

@@ -21,13 +21,13 @@ from .build import LIB, build as build_library
 
 __all__ = [
     "load", "precompute_W", "apply_M", "bicgstab", "true_residual", "W_expand", "launch_count",
-    "strerror", "OKError", "WHandle", "F64", "F32", "W_F64", "W_F32", "W_DF64", "SOLVE_AUTO", "SOLVE_F64",
-    "SOLVE_MIXED", "header_functions", "trace_enable", "trace_read", "trace_reset", "true_residual_static",
+    "strerror", "OKError", "WHandle", "F64", "F32", "F32_W16", "W_F64", "W_F32", "W_DF64", "W_F16",
+    "SOLVE_AUTO", "SOLVE_F64", "SOLVE_MIXED", "SOLVE_MIXED16", "header_functions", "trace_enable", "trace_read", "trace_reset", "true_residual_static",
 ]
 
-F64, F32 = 0, 1
-W_F64, W_F32, W_DF64 = 1, 2, 4
-SOLVE_AUTO, SOLVE_F64, SOLVE_MIXED = 0, 1, 2
+F64, F32, F32_W16 = 0, 1, 2
+W_F64, W_F32, W_DF64, W_F16 = 1, 2, 4, 8
+SOLVE_AUTO, SOLVE_F64, SOLVE_MIXED, SOLVE_MIXED16 = 0, 1, 2, 3
 OK_ENOCONV, OK_EBREAKDOWN = -4, -5
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ok.h")
 
@@ -231,8 +231,9 @@ def _field_check(W: WHandle, t, name):
         raise ValueError(f"{name} must hold V * 12 = {W.volume * 12} complex numbers")
 
 
-def apply_M(W: WHandle, psi, out=None, stream=None):
-    """ok_apply_M: out = M psi in the precision of psi (complex128 -> FP64, complex64 -> FP32)."""
+def apply_M(W: WHandle, psi, out=None, stream=None, prec=None):
+    """ok_apply_M: out = M psi in the precision of psi (complex128 -> FP64, complex64 -> FP32).
+    prec=F32_W16 (complex64 fields) applies with the half-precision W copy."""
     import torch
     _field_check(W, psi, "psi")
     if out is None:
@@ -240,7 +241,10 @@ def apply_M(W: WHandle, psi, out=None, stream=None):
     _field_check(W, out, "out")
     if out.dtype != psi.dtype:
         raise ValueError("out and psi must have the same dtype")
-    prec = F64 if psi.dtype == torch.complex128 else F32
+    if prec is None:
+        prec = F64 if psi.dtype == torch.complex128 else F32
+    elif (prec == F64) != (psi.dtype == torch.complex128):
+        raise ValueError("prec does not match the dtype of psi")
     st = load().ok_apply_M(W.ptr, prec, ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                            _stream(stream))
     _check(st, "ok_apply_M")

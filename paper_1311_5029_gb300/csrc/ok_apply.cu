@@ -150,6 +150,20 @@ __device__ __forceinline__ M3<R> wmat(const cx<R>* __restrict__ W, int site, int
   return a;
 }
 
+// Matrix m of the site record of `site` from the half-precision copy, widened to FP32.
+__device__ __forceinline__ M3<float> wmat(const cx<__half>* __restrict__ W, int site, int m) {
+  const size_t base = ((size_t)(site >> 5) * NMAT + m) * (9 * LANES) + (site & 31);
+  const unsigned* p = reinterpret_cast<const unsigned*>(W) + base;
+  M3<float> a;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    const unsigned u = __ldg(p + e * LANES);
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u));
+    a.e[e] = mk<float>(f.x, f.y);
+  }
+  return a;
+}
+
 // ---------------------------------------------------------------------------- colour algebra
 // y += A v, y -= A v, y += A^dag v, y -= A^dag v
 template <typename R> __device__ __forceinline__ void mv_add(cx<R> (&y)[3], const M3<R>& A, const cx<R> (&v)[3]) {
@@ -607,8 +621,8 @@ __device__ __forceinline__ int gather_pair(const cx<R>* __restrict__ psi, const 
   return n;
 }
 
-template <typename R, bool DAG>
-__device__ __forceinline__ void block2h(const cx<R>* __restrict__ W, int site, int m, const H6<R>& h, H6<R>& acc) {
+template <typename R, bool DAG, typename WT>
+__device__ __forceinline__ void block2h(const cx<WT>* __restrict__ W, int site, int m, const H6<R>& h, H6<R>& acc) {
   M3<R> b;
   b = wmat(W, site, m + 0);
   if (DAG) mdv_add(acc.v[0], b, h.v[0]); else mv_add(acc.v[0], b, h.v[0]);
@@ -645,25 +659,25 @@ __device__ __forceinline__ void colour2h(H6<R>& y, const M3<R>& V, const H6<R>& 
 
 // Each hop function takes FWD / BWD flags so that the forward and the backward halves of the
 // stencil can run in different warps (the split kernel below).
-template <typename R, int I, bool FWD = true, bool BWD = true>
-__device__ __forceinline__ void pair_spatial(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+template <typename R, int I, bool FWD = true, bool BWD = true, typename WT = R>
+__device__ __forceinline__ void pair_spatial(const cx<WT>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
                                              const Geom& g, int s, const Pair& pr, H6<R>& acc) {
   const int base = M_WP + 8 * I;
   H6<R> h;
   if constexpr (FWD) {
     gather_pair<R, I == 0, I == 1, I == 2, 0>(psi, c, g, pr, h);
-    block2h<R, false>(W, s, base + 4 * pr.p, h, acc);
+    block2h<R, false, WT>(W, s, base + 4 * pr.p, h, acc);
   }
   if constexpr (BWD) {
     int n = gather_pair<R, -(I == 0), -(I == 1), -(I == 2), 0>(psi, c, g, pr, h);
-    block2h<R, true>(W, n, base + 4 * (1 - pr.p), h, acc);
+    block2h<R, true, WT>(W, n, base + 4 * (1 - pr.p), h, acc);
   }
 }
 
 // acc+ += S h+ - U l (p = 0);  acc- += -S h- + U l (p = 1)   [forward, matrices at x]
 // acc+ += -U^dag u - S^dag h+;  acc- += -U^dag u + S^dag h-   [backward, matrices at x - t]
-template <typename R, bool FWD = true, bool BWD = true>
-__device__ __forceinline__ void pair_time(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+template <typename R, bool FWD = true, bool BWD = true, typename WT = R>
+__device__ __forceinline__ void pair_time(const cx<WT>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
                                           const Geom& g, int s, const Pair& pr, H6<R>& acc) {
   const R sg = pr.p ? R(-1) : R(1);
   H6<R> h, u, l;
@@ -729,8 +743,8 @@ __device__ __forceinline__ void add_scaled_h(H6<R>& acc, R a, const H6<R>& y) {
 }
 
 // W^{++}_ii: acc+- += (a +- b sigma_i) V h+-  forward,  (a -+ b sigma_i) V^dag h+-  backward.
-template <typename R, int I, bool FWD = true, bool BWD = true>
-__device__ __forceinline__ void pair_two(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+template <typename R, int I, bool FWD = true, bool BWD = true, typename WT = R>
+__device__ __forceinline__ void pair_two(const cx<WT>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
                                          const Geom& g, int s, const Pair& pr, R a, R b, H6<R>& acc) {
   const R sb = pr.p ? -b : b;
   H6<R> h, y;
@@ -752,8 +766,8 @@ __device__ __forceinline__ void pair_two(const cx<R>* __restrict__ W, const cx<R
 
 // Diagonal pair (I, J): acc+- += +-(s_I + s_J) V h, -+(s_I + s_J) V^dag h (x-I-J),
 //                       +-(s_I - s_J) X h (x+I-J), -+(s_I - s_J) X^dag h (x-I+J).
-template <typename R, int I, int J, int P, bool FWD = true, bool BWD = true>
-__device__ __forceinline__ void pair_diag(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+template <typename R, int I, int J, int P, bool FWD = true, bool BWD = true, typename WT = R>
+__device__ __forceinline__ void pair_diag(const cx<WT>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
                                           const Geom& g, int s, const Pair& pr, H6<R>& acc) {
   constexpr int A0 = (I == 0) + (J == 0), A1 = (I == 1) + (J == 1), A2 = (I == 2) + (J == 2);
   constexpr int B0 = (I == 0) - (J == 0), B1 = (I == 1) - (J == 1), B2 = (I == 2) - (J == 2);
@@ -915,8 +929,8 @@ constexpr int SPLIT_SITES = 32;
 #endif
 template <int EPI> constexpr int split_minb() { return EPI == EPI_NONE ? OK_SPLIT_MINB : OK_SPLIT_MINB_EPI; }
 
-template <typename R, int EPI>
-__global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB : OK_SPLIT_MINB_EPI) apply_split_kernel(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi,
+template <typename R, int EPI, typename WT = R>
+__global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB : OK_SPLIT_MINB_EPI) apply_split_kernel(const cx<WT>* __restrict__ W, const cx<R>* __restrict__ psi,
                                                                                    cx<R>* __restrict__ out, Geom g, R c0q, R a_ii, R b_ii,
                                                                                    EpiArgs<R> ep) {
   if (EPI != EPI_NONE && ep.halt && *ep.halt) return;
@@ -1126,6 +1140,30 @@ int launch_apply(const ok_W* Wh, const cx<R>* psi, cx<R>* out, int epi, const Ep
 
 // Upper bound of the grid size of any apply variant (sizes the reduction partials).
 int apply_blocks_needed(const ok_W* Wh) { return grid_for(Wh->g.V, SPLIT_SITES); }
+
+// FP32 fields and arithmetic with the half-precision copy of W (split kernel, all epilogues).
+int launch_apply_w16(const ok_W* Wh, const cx<float>* psi, cx<float>* out, int epi, const EpiArgs<float>& ep, cudaStream_t st) {
+  const cx<__half>* W = (const cx<__half>*)Wh->W16;
+  if (!W) return OK_EINVAL;
+  if (epi < EPI_NONE || epi > EPI_RESID) return OK_EINVAL;
+  const Geom& g = Wh->g;
+  const float c0q = (float)Wh->sc.c0q, a = (float)Wh->sc.a_ii, b = (float)Wh->sc.b_ii;
+  const int tiles = grid_for(g.V, SPLIT_SITES);
+  static const char* names[4] = {"apply_w16", "apply_w16_dot", "apply_w16_ts", "apply_w16_resid"};
+  {
+    TraceScope ts(names[epi], st);
+    const int res0 = sm_count() * split_minb<EPI_NONE>(), res1 = sm_count() * split_minb<EPI_DOT>();
+    const int g0 = tiles < res0 ? tiles : res0, g1 = tiles < res1 ? tiles : res1;
+    switch (epi) {
+      case EPI_NONE: apply_split_kernel<float, EPI_NONE, __half><<<g0, SPLIT_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+      case EPI_DOT: apply_split_kernel<float, EPI_DOT, __half><<<g1, SPLIT_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+      case EPI_TS: apply_split_kernel<float, EPI_TS, __half><<<g1, SPLIT_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+      default: apply_split_kernel<float, EPI_RESID, __half><<<g1, SPLIT_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+    }
+  }
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
 
 // FP64-accurate application with the double-float copy of W: psi in double-float, out in FP64;
 // EPI_NONE or EPI_RESID (b in FP64).  One thread per site, as for native FP64.

@@ -86,6 +86,7 @@ void ok_free_W(ok_W* W) {
   if (W->W64) cudaFree(W->W64);
   if (W->W32) cudaFree(W->W32);
   if (W->Wdf) cudaFree(W->Wdf);
+  if (W->W16) cudaFree(W->W16);
   delete W;
 }
 
@@ -103,7 +104,7 @@ int ok_W_info(const ok_W* W, ok_lattice* lat, int* W_precs, size_t* bytes) {
 
 int ok_apply_M(const ok_W* W, ok_prec prec, const void* psi, void* out, void* stream) {
   if (!W || !psi || !out) return OK_EINVAL;
-  size_t es = prec == OK_F64 ? 16 : prec == OK_F32 ? 8 : 0;
+  size_t es = prec == OK_F64 ? 16 : (prec == OK_F32 || prec == OK_F32_W16) ? 8 : 0;
   if (es == 0) return OK_EINVAL;
   size_t bytes = (size_t)W->g.V * 12 * es;
   const char* a = (const char*)psi;
@@ -129,8 +130,12 @@ int ok_apply_M(const ok_W* W, ok_prec prec, const void* psi, void* out, void* st
     if (rc == OK_SUCCESS && fe != cudaSuccess) { set_cuda_error(fe); rc = OK_ECUDA; }
     return rc;
   }
-  if (!W->W32) return OK_EINVAL;
   EpiArgs<float> e{};
+  if (prec == OK_F32_W16) {
+    if (!W->W16) return OK_EINVAL;
+    return launch_apply_w16(W, (const cx<float>*)psi, (cx<float>*)out, EPI_NONE, e, (cudaStream_t)stream);
+  }
+  if (!W->W32) return OK_EINVAL;
   return launch_apply<float>(W, (const cx<float>*)psi, (cx<float>*)out, EPI_NONE, e, (cudaStream_t)stream);
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <stddef.h>
 #include <math.h>
+#include <cuda_fp16.h>
 
 #include "../../include/ok.h"
 
@@ -180,6 +181,7 @@ struct ok_W {
   void* W64;     // cx<double>[nblk * SITE_ELEMS * 32]
   void* W32;     // cx<float>[...]
   void* Wdf;     // cx<dd>[...]: FP64-accurate double-float copy
+  void* W16;     // cx<__half>[...]: half-precision copy
   size_t bytes;
   int device;
 };

@@ -179,6 +179,7 @@ struct WOut {
   cx<double>* W64;
   cx<float>* W32;
   cx<dd>* Wdf;
+  cx<__half>* W16;
 };
 
 __device__ __forceinline__ void store_mat(const WOut& o, int site, int m, const M3<double>& a) {
@@ -190,6 +191,7 @@ __device__ __forceinline__ void store_mat(const WOut& o, int site, int m, const 
     if (o.W64) o.W64[base + (size_t)e * LANES] = a.e[e];
     if (o.W32) o.W32[base + (size_t)e * LANES] = mk<float>((float)a.e[e].re, (float)a.e[e].im);
     if (o.Wdf) o.Wdf[base + (size_t)e * LANES] = mk<dd>(dd(a.e[e].re), dd(a.e[e].im));
+    if (o.W16) o.W16[base + (size_t)e * LANES] = mk<__half>(__float2half_rn((float)a.e[e].re), __float2half_rn((float)a.e[e].im));
   }
 }
 
@@ -493,7 +495,7 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
     scalars_kernel<<<1, 256, 0, st>>>(part, nb1, g, *c, dsc);
   }
   OK_LAUNCH_CHECK();
-  WOut o{(cx<double>*)W->W64, (cx<float>*)W->W32, (cx<dd>*)W->Wdf};
+  WOut o{(cx<double>*)W->W64, (cx<float>*)W->W32, (cx<dd>*)W->Wdf, (cx<__half>*)W->W16};
   int nb2 = grid_for(g.V, K2_THREADS);
   for (int part_id = 0; part_id < 5; ++part_id) {
     {
@@ -509,7 +511,7 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
                int precs, cudaStream_t st, ok_W** W_out) {
   if (!lat || !links || !c || !W_out) return OK_EINVAL;
   if (links_prec != OK_F64 && links_prec != OK_F32) return OK_EINVAL;
-  if (precs <= 0 || (precs & ~(OK_W_F64 | OK_W_F32 | OK_W_DF64))) return OK_EINVAL;
+  if (precs <= 0 || (precs & ~(OK_W_F64 | OK_W_F32 | OK_W_DF64 | OK_W_F16))) return OK_EINVAL;
   if (!(c->u0 > 0.0) && c->u0 > 0.0) return OK_EINVAL;
   *W_out = nullptr;
   Geom g;
@@ -532,6 +534,7 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
     if (W->W64) cudaFree(W->W64);
     if (W->W32) cudaFree(W->W32);
     if (W->Wdf) cudaFree(W->Wdf);
+    if (W->W16) cudaFree(W->W16);
     delete W;
     return code;
   };
@@ -554,8 +557,14 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
     e = cudaMemsetAsync(W->Wdf, 0, elems * sizeof(cx<dd>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
   }
+  if (precs & OK_W_F16) {
+    e = cudaMalloc(&W->W16, elems * sizeof(cx<__half>));
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
+    e = cudaMemsetAsync(W->W16, 0, elems * sizeof(cx<__half>), st);
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
+  }
   W->bytes = (W->W64 ? elems * sizeof(cx<double>) : 0) + (W->W32 ? elems * sizeof(cx<float>) : 0) +
-             (W->Wdf ? elems * sizeof(cx<dd>) : 0);
+             (W->Wdf ? elems * sizeof(cx<dd>) : 0) + (W->W16 ? elems * sizeof(cx<__half>) : 0);
   int nb1 = grid_for(g.V, K1_THREADS);
   e = cudaMalloc(&EB, (size_t)g.V * 6 * 9 * sizeof(cx<double>));
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
@@ -580,7 +589,7 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
 
 int expand(const ok_W* W, ok_prec prec, int kind, void* out, cudaStream_t st) {
   if (!W || !out || kind < 0 || kind > 13) return OK_EINVAL;
-  const void* src = prec == OK_F64 ? (W->W64 ? W->W64 : W->Wdf) : prec == OK_F32 ? W->W32 : nullptr;
+  const void* src = prec == OK_F64 ? (W->W64 ? W->W64 : W->Wdf) : prec == OK_F32 ? W->W32 : prec == OK_F32_W16 ? W->W16 : nullptr;
   if (!src) return OK_EINVAL;
   WScalars* dsc = nullptr;
   OK_CUDA_TRY(cudaMallocAsync((void**)&dsc, sizeof(WScalars), st));
@@ -592,6 +601,8 @@ int expand(const ok_W* W, ok_prec prec, int kind, void* out, cudaStream_t st) {
     expand_kernel<dd><<<nb, 64, 0, st>>>((const cx<dd>*)src, W->g, dsc, kind, (cx<double>*)out);
   else if (prec == OK_F64)
     expand_kernel<double><<<nb, 64, 0, st>>>((const cx<double>*)src, W->g, dsc, kind, (cx<double>*)out);
+  else if (prec == OK_F32_W16)
+    expand_kernel<__half><<<nb, 64, 0, st>>>((const cx<__half>*)src, W->g, dsc, kind, (cx<double>*)out);
   else
     expand_kernel<float><<<nb, 64, 0, st>>>((const cx<float>*)src, W->g, dsc, kind, (cx<double>*)out);
   count_launch();

@@ -74,13 +74,23 @@ struct IterBufs {
   cx<R>* x; cx<R>* r; cx<R>* rhat; cx<R>* p; cx<R>* v; cx<R>* s; cx<R>* t;
 };
 
+// One application of M inside the iteration: with the half-precision W copy when `w16` is set
+// (FP32 fields and arithmetic), else with the copy of the iteration's precision.
 template <typename R>
-int iterate(const ok_W* W, const IterBufs<R>& b, long long n, SolverState* dst, double* part, cudaStream_t st) {
+int apply_iter(const ok_W* W, const cx<R>* psi, cx<R>* out, int epi, const EpiArgs<R>& ep, bool w16, cudaStream_t st) {
+  if constexpr (sizeof(R) == 4) {
+    if (w16) return launch_apply_w16(W, psi, out, epi, ep, st);
+  }
+  return launch_apply<R>(W, psi, out, epi, ep, st);
+}
+
+template <typename R>
+int iterate(const ok_W* W, const IterBufs<R>& b, long long n, SolverState* dst, double* part, bool w16, cudaStream_t st) {
   EpiArgs<R> e1{b.rhat, nullptr, RedArgs{dst, part, nullptr, FIN_ALPHA}, &dst->ticket[0], &dst->halt};
-  OK_TRY(launch_apply<R>(W, b.p, b.v, EPI_DOT, e1, st));
+  OK_TRY(apply_iter<R>(W, b.p, b.v, EPI_DOT, e1, w16, st));
   OK_TRY(launch_update_s<R>(b.r, b.v, b.s, n, dst, st));
   EpiArgs<R> e2{nullptr, nullptr, RedArgs{dst, part, nullptr, FIN_OMEGA}, &dst->ticket[1], &dst->halt};
-  OK_TRY(launch_apply<R>(W, b.s, b.t, EPI_TS, e2, st));
+  OK_TRY(apply_iter<R>(W, b.s, b.t, EPI_TS, e2, w16, st));
   OK_TRY(launch_update_xr<R>(b.x, b.p, b.s, b.t, b.r, b.rhat, n, dst, part, st));
   OK_TRY(launch_update_p<R>(b.p, b.r, b.v, n, dst, st));
   return OK_SUCCESS;
@@ -112,10 +122,17 @@ int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solv
   int mode = prm->mode;
   const bool has64 = W->W64 || W->Wdf;  // an FP64-accurate copy for the true residual
   if (mode == OK_SOLVE_AUTO) mode = (W->W32 && has64) ? OK_SOLVE_MIXED : OK_SOLVE_F64;
-  if (mode != OK_SOLVE_F64 && mode != OK_SOLVE_MIXED) return OK_EINVAL;
+  if (mode != OK_SOLVE_F64 && mode != OK_SOLVE_MIXED && mode != OK_SOLVE_MIXED16) return OK_EINVAL;
+  const bool w16 = mode == OK_SOLVE_MIXED16;
+  if (w16) {
+    if (!W->W16) return OK_EINVAL;
+    mode = OK_SOLVE_MIXED;  // same algorithm; the FP32 iteration reads the half-precision W
+  } else if (mode == OK_SOLVE_MIXED && !W->W32) {
+    return OK_EINVAL;
+  }
   if (mode == OK_SOLVE_F64 && !W->W64) return OK_EINVAL;  // the plain FP64 iteration uses native FP64
   if (!has64) return OK_EINVAL;
-  if (mode == OK_SOLVE_MIXED && (!W->W32 || !(prm->delta > 0.0 && prm->delta < 1.0))) return OK_EINVAL;
+  if (mode == OK_SOLVE_MIXED && !(prm->delta > 0.0 && prm->delta < 1.0)) return OK_EINVAL;
   if ((const void*)bvec == (const void*)x) return OK_EINVAL;
 
   const long long n = 12LL * W->g.V;
@@ -194,8 +211,8 @@ int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solv
 
   for (;;) {
     for (int k = 0; k < prm->check_every; ++k) {
-      if (mode == OK_SOLVE_F64) OK_TRY(iterate<double>(W, b64, n, dst, part, st));
-      else OK_TRY(iterate<float>(W, b32, n, dst, part, st));
+      if (mode == OK_SOLVE_F64) OK_TRY(iterate<double>(W, b64, n, dst, part, false, st));
+      else OK_TRY(iterate<float>(W, b32, n, dst, part, w16, st));
     }
     OK_TRY(read_state(dst, h, st));
     int halt = h->halt;

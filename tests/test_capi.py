@@ -43,7 +43,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.ok_precompute_W(ctypes.byref(zero), vp(16), 0, ctypes.byref(c), 1, None, ctypes.byref(out)) == -1
     huge = ok.ok_lattice((ctypes.c_int * 4)(1024, 1024, 1024, 4), (ctypes.c_int * 4)(1, 1, 1, 1))
     assert lib.ok_precompute_W(ctypes.byref(huge), vp(16), 0, ctypes.byref(c), 1, None, ctypes.byref(out)) == -1
-    assert lib.ok_precompute_W(ctypes.byref(lat), vp(16), 0, ctypes.byref(c), 8, None, ctypes.byref(out)) == -1
+    assert lib.ok_precompute_W(ctypes.byref(lat), vp(16), 0, ctypes.byref(c), 16, None, ctypes.byref(out)) == -1
     assert lib.ok_apply_M(None, 0, vp(16), vp(32), None) == -1
     prm = lib.ok_default_solve_params(1e-10, 100)
     info = ok.ok_solve_info()
