@@ -185,6 +185,14 @@ int ok_W_expand(const ok_W* W, ok_prec prec, int kind, void* out, void* stream);
 /* Number of kernels this library has launched since it was loaded (all devices, all threads). */
 unsigned long long ok_launch_count(void);
 
+/* Failure detection for the kernels' bounded waits.  The FP32 and FP16-W applies wait on shared-
+ * memory barriers for the bulk copies of W; a wait that has not completed after about 2^30 SM
+ * cycles gives up, so the launch ends instead of hanging, and counts itself in a device word.
+ * *n receives that count for the current device (0 unless a copy failed: then every result since
+ * the last reset is invalid); reset != 0 clears it.  Synchronous.  OK_EINVAL for a null n,
+ * OK_ECUDA if the copy fails.  The paper has no counterpart. */
+int ok_wait_timeouts(unsigned* n, int reset);
+
 /* Kernel tracing (per-kernel-class timing with CUDA events recorded on the launching stream).
  * While enabled, every kernel launch of the library is bracketed by two CUDA events; ok_trace_read
  * waits for the recorded events, folds them into per-class totals and returns up to `max` entries

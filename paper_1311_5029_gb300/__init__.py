@@ -22,7 +22,7 @@ from .build import LIB, build as build_library
 __all__ = [
     "load", "precompute_W", "apply_M", "bicgstab", "true_residual", "W_expand", "launch_count",
     "strerror", "OKError", "WHandle", "F64", "F32", "F32_W16", "W_F64", "W_F32", "W_DF64", "W_F16",
-    "SOLVE_AUTO", "SOLVE_F64", "SOLVE_MIXED", "SOLVE_MIXED16", "header_functions", "trace_enable", "trace_read", "trace_reset", "true_residual_static",
+    "SOLVE_AUTO", "SOLVE_F64", "SOLVE_MIXED", "SOLVE_MIXED16", "header_functions", "wait_timeouts", "trace_enable", "trace_read", "trace_reset", "true_residual_static",
 ]
 
 F64, F32, F32_W16 = 0, 1, 2
@@ -91,6 +91,7 @@ def load(path: str | None = None):
         "ok_true_residual_static": (i, [vp, vp, vp, vp, ctypes.POINTER(d), vp]),
         "ok_W_expand": (i, [vp, i, i, vp, vp]),
         "ok_launch_count": (ctypes.c_ulonglong, []),
+        "ok_wait_timeouts": (i, [ctypes.POINTER(ctypes.c_uint), i]),
         "ok_trace_enable": (None, [i]),
         "ok_trace_read": (i, [ctypes.POINTER(ok_trace_stat), i, ctypes.POINTER(i)]),
         "ok_trace_reset": (None, []),
@@ -119,6 +120,13 @@ def strerror(status: int) -> str:
 def launch_count() -> int:
     """Kernels launched by the library since it was loaded."""
     return int(load().ok_launch_count())
+
+
+def wait_timeouts(reset: bool = False) -> int:
+    """ok_wait_timeouts: bounded device waits that gave up (0 unless a bulk copy failed)."""
+    n = ctypes.c_uint(0)
+    _check(load().ok_wait_timeouts(ctypes.byref(n), 1 if reset else 0), "ok_wait_timeouts")
+    return int(n.value)
 
 
 def trace_enable(on: bool = True):

@@ -164,6 +164,16 @@ __device__ __forceinline__ M3<float> wmat(const cx<__half>* __restrict__ W, int 
   return a;
 }
 
+// Arithmetic type of a stored W element type (FP16 elements are widened to FP32).
+template <typename WT> struct WReal { using type = WT; };
+template <> struct WReal<__half> { using type = float; };
+
+// W source reading any site's record from global memory.
+template <typename WT> struct GlobalW {
+  const cx<WT>* __restrict__ p;
+  __device__ __forceinline__ M3<typename WReal<WT>::type> operator()(int site, int m) const { return wmat(p, site, m); }
+};
+
 // ---------------------------------------------------------------------------- colour algebra
 // y += A v, y -= A v, y += A^dag v, y -= A^dag v
 template <typename R> __device__ __forceinline__ void mv_add(cx<R> (&y)[3], const M3<R>& A, const cx<R> (&v)[3]) {
@@ -621,16 +631,16 @@ __device__ __forceinline__ int gather_pair(const cx<R>* __restrict__ psi, const 
   return n;
 }
 
-template <typename R, bool DAG, typename WT>
-__device__ __forceinline__ void block2h(const cx<WT>* __restrict__ W, int site, int m, const H6<R>& h, H6<R>& acc) {
+template <typename R, bool DAG, typename WS>
+__device__ __forceinline__ void block2h(const WS& W, int site, int m, const H6<R>& h, H6<R>& acc) {
   M3<R> b;
-  b = wmat(W, site, m + 0);
+  b = W(site, m + 0);
   if (DAG) mdv_add(acc.v[0], b, h.v[0]); else mv_add(acc.v[0], b, h.v[0]);
-  b = wmat(W, site, m + 1);
+  b = W(site, m + 1);
   if (DAG) mdv_add(acc.v[1], b, h.v[0]); else mv_add(acc.v[0], b, h.v[1]);
-  b = wmat(W, site, m + 2);
+  b = W(site, m + 2);
   if (DAG) mdv_add(acc.v[0], b, h.v[1]); else mv_add(acc.v[1], b, h.v[0]);
-  b = wmat(W, site, m + 3);
+  b = W(site, m + 3);
   if (DAG) mdv_add(acc.v[1], b, h.v[1]); else mv_add(acc.v[1], b, h.v[1]);
 }
 
@@ -659,25 +669,25 @@ __device__ __forceinline__ void colour2h(H6<R>& y, const M3<R>& V, const H6<R>& 
 
 // Each hop function takes FWD / BWD flags so that the forward and the backward halves of the
 // stencil can run in different warps (the split kernel below).
-template <typename R, int I, bool FWD = true, bool BWD = true, typename WT = R>
-__device__ __forceinline__ void pair_spatial(const cx<WT>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+template <typename R, int I, bool FWD = true, bool BWD = true, typename WS>
+__device__ __forceinline__ void pair_spatial(const WS& W, const cx<R>* __restrict__ psi, const int (&c)[4],
                                              const Geom& g, int s, const Pair& pr, H6<R>& acc) {
   const int base = M_WP + 8 * I;
   H6<R> h;
   if constexpr (FWD) {
     gather_pair<R, I == 0, I == 1, I == 2, 0>(psi, c, g, pr, h);
-    block2h<R, false, WT>(W, s, base + 4 * pr.p, h, acc);
+    block2h<R, false>(W, s, base + 4 * pr.p, h, acc);
   }
   if constexpr (BWD) {
     int n = gather_pair<R, -(I == 0), -(I == 1), -(I == 2), 0>(psi, c, g, pr, h);
-    block2h<R, true, WT>(W, n, base + 4 * (1 - pr.p), h, acc);
+    block2h<R, true>(W, n, base + 4 * (1 - pr.p), h, acc);
   }
 }
 
 // acc+ += S h+ - U l (p = 0);  acc- += -S h- + U l (p = 1)   [forward, matrices at x]
 // acc+ += -U^dag u - S^dag h+;  acc- += -U^dag u + S^dag h-   [backward, matrices at x - t]
-template <typename R, bool FWD = true, bool BWD = true, typename WT = R>
-__device__ __forceinline__ void pair_time(const cx<WT>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+template <typename R, bool FWD = true, bool BWD = true, typename WS>
+__device__ __forceinline__ void pair_time(const WS& W, const cx<R>* __restrict__ psi, const int (&c)[4],
                                           const Geom& g, int s, const Pair& pr, H6<R>& acc) {
   const R sg = pr.p ? R(-1) : R(1);
   H6<R> h, u, l;
@@ -685,16 +695,16 @@ __device__ __forceinline__ void pair_time(const cx<WT>* __restrict__ W, const cx
     gather_pair<R, 0, 0, 0, 1>(psi, c, g, pr, h, nullptr, &l);
     // acc += sg (S h - U l),  S = [[s3, n1], [n2, -s3]]
     H6<R> sh;
-    M3<R> s3 = wmat(W, s, M_ST + 0);
+    M3<R> s3 = W(s, M_ST + 0);
     mv(sh.v[0], s3, h.v[0]);
     mv(sh.v[1], s3, h.v[1]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) sh.v[1][a] = -sh.v[1][a];
-    M3<R> n1 = wmat(W, s, M_ST + 1);
+    M3<R> n1 = W(s, M_ST + 1);
     mv_add(sh.v[0], n1, h.v[1]);
-    M3<R> n2 = wmat(W, s, M_ST + 2);
+    M3<R> n2 = W(s, M_ST + 2);
     mv_add(sh.v[1], n2, h.v[0]);
-    M3<R> U = wmat(W, s, M_UT);
+    M3<R> U = W(s, M_UT);
     mv_sub(sh.v[0], U, l.v[0]);
     mv_sub(sh.v[1], U, l.v[1]);
 #pragma unroll
@@ -709,14 +719,14 @@ __device__ __forceinline__ void pair_time(const cx<WT>* __restrict__ W, const cx
     int n = gather_pair<R, 0, 0, 0, -1>(psi, c, g, pr, h, &u, nullptr);
     // S^dag h = [[s3^dag, n2^dag], [n1^dag, -s3^dag]] h ; acc += -U^dag u - sg S^dag h
     H6<R> sh;
-    M3<R> s3 = wmat(W, n, M_ST + 0);
+    M3<R> s3 = W(n, M_ST + 0);
     mdv(sh.v[0], s3, h.v[0]);
     mdv(sh.v[1], s3, h.v[1]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) sh.v[1][a] = -sh.v[1][a];
-    M3<R> n2 = wmat(W, n, M_ST + 2);
+    M3<R> n2 = W(n, M_ST + 2);
     mdv_add(sh.v[0], n2, h.v[1]);
-    M3<R> n1 = wmat(W, n, M_ST + 1);
+    M3<R> n1 = W(n, M_ST + 1);
     mdv_add(sh.v[1], n1, h.v[0]);
 #pragma unroll
     for (int q = 0; q < 2; ++q)
@@ -725,7 +735,7 @@ __device__ __forceinline__ void pair_time(const cx<WT>* __restrict__ W, const cx
         acc.v[q][a].re = fma(-sg, sh.v[q][a].re, acc.v[q][a].re);
         acc.v[q][a].im = fma(-sg, sh.v[q][a].im, acc.v[q][a].im);
       }
-    M3<R> U = wmat(W, n, M_UT);
+    M3<R> U = W(n, M_UT);
     mdv_sub(acc.v[0], U, u.v[0]);
     mdv_sub(acc.v[1], U, u.v[1]);
   }
@@ -743,21 +753,21 @@ __device__ __forceinline__ void add_scaled_h(H6<R>& acc, R a, const H6<R>& y) {
 }
 
 // W^{++}_ii: acc+- += (a +- b sigma_i) V h+-  forward,  (a -+ b sigma_i) V^dag h+-  backward.
-template <typename R, int I, bool FWD = true, bool BWD = true, typename WT = R>
-__device__ __forceinline__ void pair_two(const cx<WT>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+template <typename R, int I, bool FWD = true, bool BWD = true, typename WS>
+__device__ __forceinline__ void pair_two(const WS& W, const cx<R>* __restrict__ psi, const int (&c)[4],
                                          const Geom& g, int s, const Pair& pr, R a, R b, H6<R>& acc) {
   const R sb = pr.p ? -b : b;
   H6<R> h, y;
   if constexpr (FWD) {
     gather_pair<R, 2 * (I == 0), 2 * (I == 1), 2 * (I == 2), 0>(psi, c, g, pr, h);
-    M3<R> V = wmat(W, s, M_VII + I);
+    M3<R> V = W(s, M_VII + I);
     colour2h<R, false>(y, V, h);
     add_scaled_h(acc, a, y);
     add_sigma_h(acc, I, y, sb);
   }
   if constexpr (BWD) {
     int n = gather_pair<R, -2 * (I == 0), -2 * (I == 1), -2 * (I == 2), 0>(psi, c, g, pr, h);
-    M3<R> V = wmat(W, n, M_VII + I);
+    M3<R> V = W(n, M_VII + I);
     colour2h<R, true>(y, V, h);
     add_scaled_h(acc, a, y);
     add_sigma_h(acc, I, y, -sb);
@@ -766,8 +776,8 @@ __device__ __forceinline__ void pair_two(const cx<WT>* __restrict__ W, const cx<
 
 // Diagonal pair (I, J): acc+- += +-(s_I + s_J) V h, -+(s_I + s_J) V^dag h (x-I-J),
 //                       +-(s_I - s_J) X h (x+I-J), -+(s_I - s_J) X^dag h (x-I+J).
-template <typename R, int I, int J, int P, bool FWD = true, bool BWD = true, typename WT = R>
-__device__ __forceinline__ void pair_diag(const cx<WT>* __restrict__ W, const cx<R>* __restrict__ psi, const int (&c)[4],
+template <typename R, int I, int J, int P, bool FWD = true, bool BWD = true, typename WS>
+__device__ __forceinline__ void pair_diag(const WS& W, const cx<R>* __restrict__ psi, const int (&c)[4],
                                           const Geom& g, int s, const Pair& pr, H6<R>& acc) {
   constexpr int A0 = (I == 0) + (J == 0), A1 = (I == 1) + (J == 1), A2 = (I == 2) + (J == 2);
   constexpr int B0 = (I == 0) - (J == 0), B1 = (I == 1) - (J == 1), B2 = (I == 2) - (J == 2);
@@ -776,18 +786,18 @@ __device__ __forceinline__ void pair_diag(const cx<WT>* __restrict__ W, const cx
   M3<R> V;
   if constexpr (FWD) {
     gather_pair<R, A0, A1, A2, 0>(psi, c, g, pr, h);
-    V = wmat(W, s, M_VIJ + P);
+    V = W(s, M_VIJ + P);
     colour2h<R, false>(y, V, h); add_sigma_h(acc, I, y, sg); add_sigma_h(acc, J, y, sg);
     gather_pair<R, B0, B1, B2, 0>(psi, c, g, pr, h);
-    V = wmat(W, s, M_XIJ + P);
+    V = W(s, M_XIJ + P);
     colour2h<R, false>(y, V, h); add_sigma_h(acc, I, y, sg); add_sigma_h(acc, J, y, -sg);
   }
   if constexpr (BWD) {
     int n = gather_pair<R, -A0, -A1, -A2, 0>(psi, c, g, pr, h);
-    V = wmat(W, n, M_VIJ + P);
+    V = W(n, M_VIJ + P);
     colour2h<R, true>(y, V, h); add_sigma_h(acc, I, y, -sg); add_sigma_h(acc, J, y, -sg);
     n = gather_pair<R, -B0, -B1, -B2, 0>(psi, c, g, pr, h);
-    V = wmat(W, n, M_XIJ + P);
+    V = W(n, M_XIJ + P);
     colour2h<R, true>(y, V, h); add_sigma_h(acc, I, y, -sg); add_sigma_h(acc, J, y, sg);
   }
 }
@@ -844,16 +854,17 @@ __global__ void __launch_bounds__(APPLY_THREADS, OK_APPLY_MINB) apply_pair_kerne
 #pragma unroll
         for (int k = 0; k < 3; ++k) acc.v[q][k] = (Rm.v[q][k] + Rp.v[q][k]) + ti(Rm.v[q][k] - Rp.v[q][k]);
     }
-    pair_spatial<R, 0>(W, psi, c, g, s, pr, acc);
-    pair_spatial<R, 1>(W, psi, c, g, s, pr, acc);
-    pair_spatial<R, 2>(W, psi, c, g, s, pr, acc);
-    pair_time<R>(W, psi, c, g, s, pr, acc);
-    pair_two<R, 0>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
-    pair_two<R, 1>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
-    pair_two<R, 2>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
-    pair_diag<R, 0, 1, 0>(W, psi, c, g, s, pr, acc);
-    pair_diag<R, 0, 2, 1>(W, psi, c, g, s, pr, acc);
-    pair_diag<R, 1, 2, 2>(W, psi, c, g, s, pr, acc);
+    const GlobalW<R> Wg{W};
+    pair_spatial<R, 0>(Wg, psi, c, g, s, pr, acc);
+    pair_spatial<R, 1>(Wg, psi, c, g, s, pr, acc);
+    pair_spatial<R, 2>(Wg, psi, c, g, s, pr, acc);
+    pair_time<R>(Wg, psi, c, g, s, pr, acc);
+    pair_two<R, 0>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+    pair_two<R, 1>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+    pair_two<R, 2>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+    pair_diag<R, 0, 1, 0>(Wg, psi, c, g, s, pr, acc);
+    pair_diag<R, 0, 2, 1>(Wg, psi, c, g, s, pr, acc);
+    pair_diag<R, 1, 2, 2>(Wg, psi, c, g, s, pr, acc);
 
     // out_u = acc+ + acc- (p = 0 writes it), out_l = acc+ - acc- (p = 1)
     H6<R> ap = partner(acc, pr.mask), o;
@@ -915,11 +926,21 @@ __global__ void __launch_bounds__(APPLY_THREADS, OK_APPLY_MINB) apply_pair_kerne
 // hands its partial sums over through shared memory.  Each thread's chain of dependent
 // load-then-multiply rounds is half as long as in the pair kernel, so twice as many global loads
 // are in flight per resident site.
+//
+// Staged form (STAGED = true): the forward half reads its own tile's W record from shared memory.
+// The record of a 32-site tile is contiguous in the site-blocked layout, so the Tensor Memory
+// Accelerator streams it (cp.async.bulk: one thread issues, an mbarrier counts the bytes) in
+// NCHUNK chunks, one per group of hops, through OK_STAGES shared-memory slots.  The copy of chunk
+// q + OK_STAGES is issued as soon as both forward warps are done with chunk q, across the block's
+// tiles, so the DRAM stream of W is kept in flight by the copy engine instead of by registers.
+// The backward half gathers the neighbours' matrices with ordinary loads: the block that owns
+// that tile streamed them shortly before, so they are L2 hits.
 constexpr int SPLIT_THREADS = 128;
 constexpr int SPLIT_SITES = 32;
+static_assert(SPLIT_SITES == LANES, "a tile is one site block of the W layout");
 
-// 4 resident blocks per SM (128 registers per thread): measured best on 16^3 x 32 (102 us against
-// 119 us with 2 blocks and 117 us with 5).
+// 4 resident blocks per SM (128 registers per thread): measured best on 16^3 x 32 for the
+// unstaged form (102 us against 119 us with 2 blocks and 117 us with 5).
 #ifndef OK_SPLIT_MINB
 #define OK_SPLIT_MINB 4
 #endif
@@ -927,9 +948,135 @@ constexpr int SPLIT_SITES = 32;
 #ifndef OK_SPLIT_MINB_EPI
 #define OK_SPLIT_MINB_EPI 4
 #endif
-template <int EPI> constexpr int split_minb() { return EPI == EPI_NONE ? OK_SPLIT_MINB : OK_SPLIT_MINB_EPI; }
 
-template <typename R, int EPI, typename WT = R>
+#ifndef OK_STAGES
+#define OK_STAGES 2
+#endif
+constexpr int NCHUNK = 7;     // W0 | W+t | W+x | W+y | W+z | W++ii | W++ij, W+-ij
+constexpr int CHUNK_MAX = 8;  // matrices in the largest chunk
+__device__ __forceinline__ int chunk_first(int c) {
+  return c == 0 ? M_Y0P : c == 1 ? M_UT : c == 5 ? M_VII : c == 6 ? M_VIJ : M_WP + 8 * (c - 2);
+}
+__device__ __forceinline__ int chunk_count(int c) { return c == 0 ? 6 : c == 1 ? 4 : c == 5 ? 3 : c == 6 ? 6 : 8; }
+// A staged matrix occupies its own 9 x 32 elements plus 16 bytes: the two threads of a pair read
+// matrices 4 apart, which this shift puts in different shared-memory banks.
+template <typename WT> constexpr int smat_elems() { return 9 * LANES + 16 / (int)sizeof(cx<WT>); }
+template <typename WT> constexpr int slot_elems() { return CHUNK_MAX * smat_elems<WT>(); }
+template <typename WT> constexpr size_t staged_smem() { return (size_t)OK_STAGES * slot_elems<WT>() * sizeof(cx<WT>); }
+
+// Bounded waits: a wait that has not completed after about 2^30 SM cycles (half a second) gives
+// up, counts itself here and lets the kernel run to its end (the result is then invalid).
+__device__ unsigned g_wait_timeouts;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1LL << 30)) {
+      atomicAdd(&g_wait_timeouts, 1u);
+      return false;
+    }
+  }
+  return true;
+}
+// Global -> shared bulk copy completing on `bar` (both addresses 16-byte aligned, bytes % 16 == 0).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// Named barrier 1 over the 64 forward threads (non-aligned form: lanes may arrive diverged).
+__device__ __forceinline__ void fwd_bar_sync() { asm volatile("barrier.sync 1, 64;" ::: "memory"); }
+
+// W source reading the tile's own matrices [m0, m0 + count) from a staged chunk.
+template <typename WT> struct StagedW {
+  const cx<WT>* slot;
+  int m0;
+  __device__ __forceinline__ M3<typename WReal<WT>::type> operator()(int site, int m) const {
+    const cx<WT>* q = slot + (m - m0) * smat_elems<WT>() + (site & (LANES - 1));
+    M3<typename WReal<WT>::type> a;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      if constexpr (std::is_same<WT, __half>::value) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(q + e * LANES));
+        a.e[e] = mk<float>(f.x, f.y);
+      } else if constexpr (std::is_same<WT, float>::value) {
+        const float2 f = *reinterpret_cast<const float2*>(q + e * LANES);
+        a.e[e] = mk<float>(f.x, f.y);
+      } else {
+        const double2 f = *reinterpret_cast<const double2*>(q + e * LANES);
+        a.e[e] = mk<double>(f.x, f.y);
+      }
+    }
+    return a;
+  }
+};
+
+// Issue the copies of chunk q of this block (tile blockIdx.x + (q / NCHUNK) gridDim.x) into slot
+// q % OK_STAGES.  Called by one thread.
+template <typename WT>
+__device__ __forceinline__ void issue_chunk(const cx<WT>* __restrict__ W, cx<WT>* stage, unsigned long long* full, int q) {
+  const int tile = blockIdx.x + (q / NCHUNK) * gridDim.x;
+  const int c = q % NCHUNK, slot = q % OK_STAGES;
+  const int m0 = chunk_first(c), n = chunk_count(c);
+  constexpr unsigned mbytes = 9 * LANES * sizeof(cx<WT>);
+  // The slot was last read through the generic proxy; order those reads before the async writes.
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(&full[slot], n * mbytes);
+  for (int j = 0; j < n; ++j)
+    bulk_g2s(stage + (size_t)slot * slot_elems<WT>() + (size_t)j * smat_elems<WT>(),
+             W + ((size_t)tile * NMAT + m0 + j) * (9 * LANES), mbytes, &full[slot]);
+}
+
+// On-site term W^0 psi_x (both halves of the pair): p = 0 forms A = Y+ (u - i l), p = 1 forms
+// B = Y- (u + i l); acc = (A + B) + i (A - B) for p = 0 and (A + B) - i (A - B) for p = 1.
+template <typename R, typename WS>
+__device__ __forceinline__ void pair_onsite(const WS& W, const cx<R>* __restrict__ psi, int s, const Pair& pr, R c0q,
+                                            H6<R>& acc) {
+  H6<R> mine, oth, v, Rm;
+  load_half<R>(psi, s, pr.p, mine);
+  oth = partner(mine, pr.mask);
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cx<R> u = pr.p ? oth.v[q][k] : mine.v[q][k];
+      cx<R> l = pr.p ? mine.v[q][k] : oth.v[q][k];
+      v.v[q][k] = pr.p ? u + ti(l) : u - ti(l);
+      Rm.v[q][k] = c0q * v.v[q][k];
+    }
+  const int m0 = pr.p ? M_Y0M : M_Y0P;
+  M3<R> y = W(s, m0 + 0);
+  mv_add(Rm.v[0], y, v.v[0]); mv_sub(Rm.v[1], y, v.v[1]);
+  y = W(s, m0 + 1);
+  mv_add(Rm.v[0], y, v.v[1]);
+  y = W(s, m0 + 2);
+  mv_add(Rm.v[1], y, v.v[0]);
+  H6<R> Rp = partner(Rm, pr.mask);
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc.v[q][k] = (Rm.v[q][k] + Rp.v[q][k]) + ti(Rm.v[q][k] - Rp.v[q][k]);
+}
+
+template <typename R, int EPI, typename WT, bool STAGED>
 __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB : OK_SPLIT_MINB_EPI) apply_split_kernel(const cx<WT>* __restrict__ W, const cx<R>* __restrict__ psi,
                                                                                    cx<R>* __restrict__ out, Geom g, R c0q, R a_ii, R b_ii,
                                                                                    EpiArgs<R> ep) {
@@ -940,91 +1087,123 @@ __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB
   // only after it has read buffer (k - 2) & 1 = k & 1.
   __shared__ cx<R> xch[2][64][6];
   __shared__ cx<R> xev[EPI == EPI_NONE ? 1 : 2][64][6];
+  __shared__ __align__(8) unsigned long long full[STAGED ? OK_STAGES : 1];
+  extern __shared__ __align__(128) unsigned char stage_raw[];
+  cx<WT>* stage = reinterpret_cast<cx<WT>*>(stage_raw);
   const int half = threadIdx.x >> 6;  // warp-uniform: 0 forward, 1 backward
   const int t = threadIdx.x & 63;
   Pair pr;
   pr.p = t & 1;
   pr.mask = 3u << (threadIdx.x & 30);
+  const GlobalW<WT> Wg{W};
   // Per-thread partial sums over this thread's few sites stay in the field's precision (fewer
   // registers); the block and grid reductions that follow are FP64.
   R red[3] = {0, 0, 0};
   const int ntiles = (g.V + SPLIT_SITES - 1) / SPLIT_SITES;
+  const int nq = (STAGED && (int)blockIdx.x < ntiles) ? ((ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1) * NCHUNK : 0;
+  int qc = 0;  // next chunk (forward warps)
+  bool staged_ok = true;
+  if constexpr (STAGED) {
+    if (threadIdx.x == 0) {
+      for (int k = 0; k < OK_STAGES; ++k) mbar_init(&full[k], 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int k = 0; k < OK_STAGES && k < nq; ++k) issue_chunk<WT>(W, stage, full, k);
+  }
+  // Wait for chunk qc; the forward warps then read it through a StagedW.
+  auto chunk = [&](int m0) {
+    const int slot = qc % OK_STAGES;
+    if (staged_ok) staged_ok = mbar_wait(&full[slot], (qc / OK_STAGES) & 1);
+    return StagedW<WT>{stage + (size_t)slot * slot_elems<WT>(), m0};
+  };
+  // Both forward warps are done with chunk qc: its slot takes chunk qc + OK_STAGES.
+  auto release = [&]() {
+    fwd_bar_sync();
+    if (threadIdx.x == 0 && qc + OK_STAGES < nq) issue_chunk<WT>(W, stage, full, qc + OK_STAGES);
+    ++qc;
+  };
   int kb = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, kb ^= 1) {
   const int s = tile * SPLIT_SITES + (t >> 1);
   const bool active = s < g.V;
   H6<R> acc;
 #pragma unroll
-  for (int q = 0; q < 2; ++q)
+  for (int qq = 0; qq < 2; ++qq)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) acc.v[q][k] = mk<R>(0, 0);
+    for (int k = 0; k < 3; ++k) acc.v[qq][k] = mk<R>(0, 0);
   int c[4] = {0, 0, 0, 0};
   if (active) {
     int r = s;
     c[0] = r % g.L[0]; r /= g.L[0];
     c[1] = r % g.L[1]; r /= g.L[1];
     c[2] = r % g.L[2]; c[3] = r / g.L[2];
-    if (half == 0) {
-      H6<R> mine, oth, v, Rm;
-      load_half<R>(psi, s, pr.p, mine);
-      oth = partner(mine, pr.mask);
-#pragma unroll
-      for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          cx<R> u = pr.p ? oth.v[q][k] : mine.v[q][k];
-          cx<R> l = pr.p ? mine.v[q][k] : oth.v[q][k];
-          v.v[q][k] = pr.p ? u + ti(l) : u - ti(l);
-          Rm.v[q][k] = c0q * v.v[q][k];
+  }
+  if (half == 0) {
+    if constexpr (STAGED) {
+      // Every forward thread takes part in the waits and barriers, active or not.
+      { auto w = chunk(M_Y0P); if (active) pair_onsite<R>(w, psi, s, pr, c0q, acc); release(); }
+      { auto w = chunk(M_UT); if (active) pair_time<R, true, false>(w, psi, c, g, s, pr, acc); release(); }
+      { auto w = chunk(M_WP + 0); if (active) pair_spatial<R, 0, true, false>(w, psi, c, g, s, pr, acc); release(); }
+      { auto w = chunk(M_WP + 8); if (active) pair_spatial<R, 1, true, false>(w, psi, c, g, s, pr, acc); release(); }
+      { auto w = chunk(M_WP + 16); if (active) pair_spatial<R, 2, true, false>(w, psi, c, g, s, pr, acc); release(); }
+      {
+        auto w = chunk(M_VII);
+        if (active) {
+          pair_two<R, 0, true, false>(w, psi, c, g, s, pr, a_ii, b_ii, acc);
+          pair_two<R, 1, true, false>(w, psi, c, g, s, pr, a_ii, b_ii, acc);
+          pair_two<R, 2, true, false>(w, psi, c, g, s, pr, a_ii, b_ii, acc);
         }
-      const int m0 = pr.p ? M_Y0M : M_Y0P;
-      M3<R> y = wmat(W, s, m0 + 0);
-      mv_add(Rm.v[0], y, v.v[0]); mv_sub(Rm.v[1], y, v.v[1]);
-      y = wmat(W, s, m0 + 1);
-      mv_add(Rm.v[0], y, v.v[1]);
-      y = wmat(W, s, m0 + 2);
-      mv_add(Rm.v[1], y, v.v[0]);
-      H6<R> Rp = partner(Rm, pr.mask);
+        release();
+      }
+      {
+        auto w = chunk(M_VIJ);
+        if (active) {
+          pair_diag<R, 0, 1, 0, true, false>(w, psi, c, g, s, pr, acc);
+          pair_diag<R, 0, 2, 1, true, false>(w, psi, c, g, s, pr, acc);
+          pair_diag<R, 1, 2, 2, true, false>(w, psi, c, g, s, pr, acc);
+        }
+        release();
+      }
+    } else if (active) {
+      pair_onsite<R>(Wg, psi, s, pr, c0q, acc);
+      pair_spatial<R, 0, true, false>(Wg, psi, c, g, s, pr, acc);
+      pair_spatial<R, 1, true, false>(Wg, psi, c, g, s, pr, acc);
+      pair_spatial<R, 2, true, false>(Wg, psi, c, g, s, pr, acc);
+      pair_time<R, true, false>(Wg, psi, c, g, s, pr, acc);
+      pair_two<R, 0, true, false>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_two<R, 1, true, false>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_two<R, 2, true, false>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_diag<R, 0, 1, 0, true, false>(Wg, psi, c, g, s, pr, acc);
+      pair_diag<R, 0, 2, 1, true, false>(Wg, psi, c, g, s, pr, acc);
+      pair_diag<R, 1, 2, 2, true, false>(Wg, psi, c, g, s, pr, acc);
+    }
+  } else if (active) {
+      pair_spatial<R, 0, false, true>(Wg, psi, c, g, s, pr, acc);
+      pair_spatial<R, 1, false, true>(Wg, psi, c, g, s, pr, acc);
+      pair_spatial<R, 2, false, true>(Wg, psi, c, g, s, pr, acc);
+      pair_time<R, false, true>(Wg, psi, c, g, s, pr, acc);
+      pair_two<R, 0, false, true>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_two<R, 1, false, true>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_two<R, 2, false, true>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_diag<R, 0, 1, 0, false, true>(Wg, psi, c, g, s, pr, acc);
+      pair_diag<R, 0, 2, 1, false, true>(Wg, psi, c, g, s, pr, acc);
+      pair_diag<R, 1, 2, 2, false, true>(Wg, psi, c, g, s, pr, acc);
 #pragma unroll
-      for (int q = 0; q < 2; ++q)
+      for (int qq = 0; qq < 2; ++qq)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) acc.v[q][k] = (Rm.v[q][k] + Rp.v[q][k]) + ti(Rm.v[q][k] - Rp.v[q][k]);
-      pair_spatial<R, 0, true, false>(W, psi, c, g, s, pr, acc);
-      pair_spatial<R, 1, true, false>(W, psi, c, g, s, pr, acc);
-      pair_spatial<R, 2, true, false>(W, psi, c, g, s, pr, acc);
-      pair_time<R, true, false>(W, psi, c, g, s, pr, acc);
-      pair_two<R, 0, true, false>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
-      pair_two<R, 1, true, false>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
-      pair_two<R, 2, true, false>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
-      pair_diag<R, 0, 1, 0, true, false>(W, psi, c, g, s, pr, acc);
-      pair_diag<R, 0, 2, 1, true, false>(W, psi, c, g, s, pr, acc);
-      pair_diag<R, 1, 2, 2, true, false>(W, psi, c, g, s, pr, acc);
-    } else {
-      pair_spatial<R, 0, false, true>(W, psi, c, g, s, pr, acc);
-      pair_spatial<R, 1, false, true>(W, psi, c, g, s, pr, acc);
-      pair_spatial<R, 2, false, true>(W, psi, c, g, s, pr, acc);
-      pair_time<R, false, true>(W, psi, c, g, s, pr, acc);
-      pair_two<R, 0, false, true>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
-      pair_two<R, 1, false, true>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
-      pair_two<R, 2, false, true>(W, psi, c, g, s, pr, a_ii, b_ii, acc);
-      pair_diag<R, 0, 1, 0, false, true>(W, psi, c, g, s, pr, acc);
-      pair_diag<R, 0, 2, 1, false, true>(W, psi, c, g, s, pr, acc);
-      pair_diag<R, 1, 2, 2, false, true>(W, psi, c, g, s, pr, acc);
-#pragma unroll
-      for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) xch[kb][t][3 * q + k] = acc.v[q][k];
+        for (int k = 0; k < 3; ++k) xch[kb][t][3 * qq + k] = acc.v[qq][k];
       // The epilogue's own half-spinor (rhat, psi or b at this site) is fetched here, on the
       // backward warps, which would otherwise wait at the barrier for the longer forward half.
       if (EPI != EPI_NONE) {
         H6<R> ev;
         load_half<R>(EPI == EPI_DOT ? ep.rhat : EPI == EPI_RESID ? ep.b : psi, s, pr.p, ev);
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
+        for (int qq = 0; qq < 2; ++qq)
 #pragma unroll
-          for (int k = 0; k < 3; ++k) xev[kb][t][3 * q + k] = ev.v[q][k];
+          for (int k = 0; k < 3; ++k) xev[kb][t][3 * qq + k] = ev.v[qq][k];
       }
-    }
   }
   __syncthreads();
   if (half == 0 && active) {
@@ -1101,15 +1280,35 @@ __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB
 #endif
 template <typename R> constexpr int apply_variant() { return sizeof(R) == 8 ? OK_APPLY64_VARIANT : OK_APPLY32_VARIANT; }
 
+// Forward W through the staged (TMA) path in the split kernel: 1 (default) or 0.
+#ifndef OK_SPLIT_STAGED
+#define OK_SPLIT_STAGED 1
+#endif
+
+// Persistent grid of the split kernel: as many blocks as fit on the device at once (from the
+// occupancy calculator for this instantiation and its dynamic shared memory), at most one per tile.
+template <typename R, int EPI, typename WT, bool STAGED>
+static void launch_split(const cx<WT>* W, const cx<R>* psi, cx<R>* out, const Geom& g, R c0q, R a, R b,
+                         const EpiArgs<R>& ep, cudaStream_t st) {
+  static int resident = 0;
+  const size_t dyn = STAGED ? staged_smem<WT>() : 0;
+  auto kern = apply_split_kernel<R, EPI, WT, STAGED>;
+  if (resident == 0) {
+    if (dyn > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, SPLIT_THREADS, dyn) != cudaSuccess || nb < 1) nb = 1;
+    resident = nb * sm_count();
+  }
+  const int tiles = grid_for(g.V, SPLIT_SITES);
+  kern<<<tiles < resident ? tiles : resident, SPLIT_THREADS, dyn, st>>>(W, psi, out, g, c0q, a, b, ep);
+}
+
 template <typename R, int EPI>
 static void launch_variant(const cx<R>* W, const cx<R>* psi, cx<R>* out, const Geom& g, R c0q, R a, R b,
                            const EpiArgs<R>& ep, cudaStream_t st) {
   constexpr int v = apply_variant<R>();
-  if constexpr (v == 2) {
-    const int tiles = grid_for(g.V, SPLIT_SITES);
-    const int resident = sm_count() * split_minb<EPI>();
-    apply_split_kernel<R, EPI><<<tiles < resident ? tiles : resident, SPLIT_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep);
-  }
+  if constexpr (v == 2)
+    launch_split<R, EPI, R, OK_SPLIT_STAGED != 0>(W, psi, out, g, c0q, a, b, ep, st);
   else if constexpr (v == 1)
     apply_pair_kernel<R, EPI><<<grid_for(2LL * g.V, APPLY_THREADS), APPLY_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep);
   else
@@ -1148,20 +1347,28 @@ int launch_apply_w16(const ok_W* Wh, const cx<float>* psi, cx<float>* out, int e
   if (epi < EPI_NONE || epi > EPI_RESID) return OK_EINVAL;
   const Geom& g = Wh->g;
   const float c0q = (float)Wh->sc.c0q, a = (float)Wh->sc.a_ii, b = (float)Wh->sc.b_ii;
-  const int tiles = grid_for(g.V, SPLIT_SITES);
   static const char* names[4] = {"apply_w16", "apply_w16_dot", "apply_w16_ts", "apply_w16_resid"};
   {
     TraceScope ts(names[epi], st);
-    const int res0 = sm_count() * split_minb<EPI_NONE>(), res1 = sm_count() * split_minb<EPI_DOT>();
-    const int g0 = tiles < res0 ? tiles : res0, g1 = tiles < res1 ? tiles : res1;
+    constexpr bool S = OK_SPLIT_STAGED != 0;
     switch (epi) {
-      case EPI_NONE: apply_split_kernel<float, EPI_NONE, __half><<<g0, SPLIT_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-      case EPI_DOT: apply_split_kernel<float, EPI_DOT, __half><<<g1, SPLIT_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-      case EPI_TS: apply_split_kernel<float, EPI_TS, __half><<<g1, SPLIT_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
-      default: apply_split_kernel<float, EPI_RESID, __half><<<g1, SPLIT_THREADS, 0, st>>>(W, psi, out, g, c0q, a, b, ep); break;
+      case EPI_NONE: launch_split<float, EPI_NONE, __half, S>(W, psi, out, g, c0q, a, b, ep, st); break;
+      case EPI_DOT: launch_split<float, EPI_DOT, __half, S>(W, psi, out, g, c0q, a, b, ep, st); break;
+      case EPI_TS: launch_split<float, EPI_TS, __half, S>(W, psi, out, g, c0q, a, b, ep, st); break;
+      default: launch_split<float, EPI_RESID, __half, S>(W, psi, out, g, c0q, a, b, ep, st); break;
     }
   }
   OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+// Bounded waits that gave up since the last reset (see g_wait_timeouts).
+int read_wait_timeouts(unsigned* n, bool reset) {
+  if (cudaMemcpyFromSymbol(n, g_wait_timeouts, sizeof(unsigned)) != cudaSuccess) return OK_ECUDA;
+  if (reset) {
+    const unsigned zero = 0;
+    if (cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(unsigned)) != cudaSuccess) return OK_ECUDA;
+  }
   return OK_SUCCESS;
 }
 

@@ -172,6 +172,11 @@ int ok_W_expand(const ok_W* W, ok_prec prec, int kind, void* out, void* stream) 
 
 unsigned long long ok_launch_count(void) { return launches(); }
 
+int ok_wait_timeouts(unsigned* n, int reset) {
+  if (!n) return OK_EINVAL;
+  return okgb::read_wait_timeouts(n, reset != 0);
+}
+
 void ok_trace_enable(int on) { g_trace_on.store(on ? 1 : 0); }
 
 int ok_trace_read(ok_trace_stat* stats, int max, int* n) {

@@ -28,6 +28,8 @@ int apply_blocks_needed(const ok_W* W);
 int launch_apply_df(const ok_W* W, const cx<dd>* psi_df, cx<double>* out, int epi, const EpiArgs<dd>& ep, cudaStream_t st);
 // FP32 fields and arithmetic with the half-precision W copy (all epilogues).
 int launch_apply_w16(const ok_W* W, const cx<float>* psi, cx<float>* out, int epi, const EpiArgs<float>& ep, cudaStream_t st);
+// Bounded device waits that gave up (the kernel's result is then invalid); optionally reset.
+int read_wait_timeouts(unsigned* n, bool reset);
 // FP64 complex -> double-float complex (n complex numbers).
 int launch_to_df(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t st);
 

@@ -214,3 +214,18 @@ def test_double_float_16cube32_sampled():
     exp = direct.apply_at(U, c, src, sites)
     got = ok.apply_M(W, to_dev(src)).cpu().numpy().reshape(V, 4, 3)[sites]
     assert rel_max(got, exp) < 10 * FP64_TOL
+
+
+def test_staged_copies_complete():
+    """The FP32 and FP16-W applies stream W through bulk copies and bounded barrier waits; on
+    lattices with ragged last tiles and with many tiles per resident block no wait may give up."""
+    ok.wait_timeouts(reset=True)
+    for dims, seed in (((7, 6, 5, 9), 1), ((16, 16, 16, 32), 2), ((3, 5, 4, 3), 3)):
+        U = to_dev(synth.random_links(dims, 0.3, 7100 + seed))
+        W = ok.precompute_W(U, synth.random_coeffs(7200 + seed), (1, 1, 1, 1), ok.W_F32 | ok.W_F16)
+        psi = to_dev(synth.gaussian_source(dims, 7300 + seed).astype(np.complex64))
+        a = ok.apply_M(W, psi)
+        h = ok.apply_M(W, psi, prec=ok.F32_W16)
+        torch.cuda.synchronize()
+        assert torch.isfinite(torch.view_as_real(a)).all() and torch.isfinite(torch.view_as_real(h)).all()
+    assert ok.wait_timeouts() == 0
