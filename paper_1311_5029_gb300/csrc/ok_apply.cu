@@ -1294,7 +1294,8 @@ static void launch_split(const cx<WT>* W, const cx<R>* psi, cx<R>* out, const Ge
   const size_t dyn = STAGED ? staged_smem<WT>() : 0;
   auto kern = apply_split_kernel<R, EPI, WT, STAGED>;
   if (resident == 0) {
-    if (dyn > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    // Static plus dynamic shared memory above 48 KB needs the opt-in (the FP32 reducing variants).
+    if (dyn > 0) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, SPLIT_THREADS, dyn) != cudaSuccess || nb < 1) nb = 1;
     resident = nb * sm_count();
