@@ -145,6 +145,49 @@ int ok_bicgstab(const ok_W* W, const void* src, void* x, double tol, int maxiter
 int ok_bicgstab_ex(const ok_W* W, const void* src, void* x, const ok_solve_params* params,
                    ok_solve_info* info, void* stream);
 
+/* Several right-hand sides at once (the 12 spin-colour sources of a propagator; the paper's
+ * method solves one source at a time, Sec. 2.3).
+ *
+ * ok_apply_M_multi: out_k = M psi_k for k < nrhs in one launch; every W matrix a thread loads is
+ * applied to several right-hand sides (the count chosen by ok_autotune).  prec OK_F32 (FP32 W) or
+ * OK_F32_W16 (FP16 W), FP32 fields and arithmetic.
+ *   psi, out: device [nrhs][V][4][3] complex64, 16-byte aligned, not overlapping.
+ * Errors: OK_EINVAL (null, nrhs < 1, overlap, misalignment, copy missing), OK_ECUDA.  Asynchronous.
+ *
+ * ok_bicgstab_multi: solves M x_k = src_k for k < nrhs with the mixed-precision method of
+ * ok_bicgstab_ex run for all systems in lockstep: FP32 iteration on the FP32 (OK_SOLVE_MIXED) or
+ * FP16 (OK_SOLVE_MIXED16; OK_SOLVE_AUTO picks it when the handle has OK_W_F16) copy of W with
+ * FP64 reliable updates, every system to its own true FP64 residual below params->tol.  One
+ * iteration is five launches for all systems, captured once into a CUDA graph and replayed
+ * params->check_every iterations at a time.
+ *   src, x: device [nrhs][V][4][3] complex128 (x: initial guess in, solution out), 1 <= nrhs <= 64;
+ *   info: host array of nrhs records (may be NULL).
+ * Needs OK_W_F64 or OK_W_DF64 for the residuals.  Returns OK_SUCCESS when every system converged,
+ * else the first failing system's code (OK_ENOCONV, OK_EBREAKDOWN, OK_ENONFINITE); OK_EINVAL for
+ * bad arguments (including params->delta outside (0, 1)), OK_ENOMEM, OK_ECUDA. */
+int ok_apply_M_multi(const ok_W* W, ok_prec prec, int nrhs, const void* psi, void* out, void* stream);
+int ok_bicgstab_multi(const ok_W* W, int nrhs, const void* src, void* x, const ok_solve_params* params,
+                      ok_solve_info* info, void* stream);
+
+/* Autotuner: times the candidate launch shapes of the FP32 (prec OK_F32) or FP16-W (OK_F32_W16)
+ * application on scratch fields (two untimed and five timed launches each, CUDA events on
+ * `stream`) and stores the fastest in the handle, which later applies and solves use.
+ *   nrhs = 1: the single right-hand side kernel with the forward W read by ordinary loads or
+ *             streamed into shared memory by TMA; *choice = 1 if streaming won;
+ *   nrhs > 1: right-hand sides per thread (1, 2 or 4, dividing nrhs) and the persistent grid
+ *             width; *choice = the right-hand sides per thread.
+ * choice, best_us (the winner's time per launch, microseconds) may be NULL.  Synchronises
+ * `stream`; allocates 2 nrhs V 96 bytes of scratch.  Not thread-safe against concurrent use of
+ * the same handle.  OK_EINVAL for bad arguments or a missing copy, OK_ECUDA.  The paper has no
+ * counterpart. */
+int ok_autotune(ok_W* W, ok_prec prec, int nrhs, int* choice, double* best_us, void* stream);
+
+/* Pin the launch shapes of the FP32 (OK_F32) or FP16-W (OK_F32_W16) application by hand instead
+ * of measuring them: staged (0 or 1) for one right-hand side, nr (0 = default, else 1, 2 or 4
+ * right-hand sides per thread) and blocks_x (0 = as many as fit, else 1..2^20) for several.
+ * OK_EINVAL for other values. */
+int ok_set_launch_shape(ok_W* W, ok_prec prec, int staged, int nr, int blocks_x);
+
 /* The defaults used by ok_bicgstab, for the given tol and maxiter. */
 ok_solve_params ok_default_solve_params(double tol, int maxiter);
 

@@ -22,7 +22,7 @@ from .build import LIB, build as build_library
 __all__ = [
     "load", "precompute_W", "apply_M", "bicgstab", "true_residual", "W_expand", "launch_count",
     "strerror", "OKError", "WHandle", "F64", "F32", "F32_W16", "W_F64", "W_F32", "W_DF64", "W_F16",
-    "SOLVE_AUTO", "SOLVE_F64", "SOLVE_MIXED", "SOLVE_MIXED16", "header_functions", "wait_timeouts", "trace_enable", "trace_read", "trace_reset", "true_residual_static",
+    "SOLVE_AUTO", "SOLVE_F64", "SOLVE_MIXED", "SOLVE_MIXED16", "header_functions", "wait_timeouts", "apply_M_multi", "bicgstab_multi", "autotune", "set_launch_shape", "trace_enable", "trace_read", "trace_reset", "true_residual_static",
 ]
 
 F64, F32, F32_W16 = 0, 1, 2
@@ -92,6 +92,10 @@ def load(path: str | None = None):
         "ok_W_expand": (i, [vp, i, i, vp, vp]),
         "ok_launch_count": (ctypes.c_ulonglong, []),
         "ok_wait_timeouts": (i, [ctypes.POINTER(ctypes.c_uint), i]),
+        "ok_apply_M_multi": (i, [vp, i, i, vp, vp, vp]),
+        "ok_bicgstab_multi": (i, [vp, i, vp, vp, ctypes.POINTER(ok_solve_params), ctypes.POINTER(ok_solve_info), vp]),
+        "ok_autotune": (i, [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]),
+        "ok_set_launch_shape": (i, [vp, i, i, i, i]),
         "ok_trace_enable": (None, [i]),
         "ok_trace_read": (i, [ctypes.POINTER(ok_trace_stat), i, ctypes.POINTER(i)]),
         "ok_trace_reset": (None, []),
@@ -280,6 +284,69 @@ def bicgstab(W: WHandle, src, x=None, tol=1e-10, maxiter=20000, mode=SOLVE_AUTO,
     if st != 0 and (raise_on_noconv or st not in (OK_ENOCONV, OK_EBREAKDOWN)):
         raise OKError(st, "ok_bicgstab_ex")
     return x, d
+
+
+def _multi_check(W: WHandle, t, name, dtype):
+    import torch
+    _need_cuda(t, (dtype,), name)
+    if t.dim() < 1 or t.numel() % (W.volume * 12) != 0 or t.numel() == 0:
+        raise ValueError(f"{name} must hold nrhs * V * 12 complex numbers")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.numel() // (W.volume * 12)
+
+
+def apply_M_multi(W: WHandle, psi, out=None, prec=F32, stream=None):
+    """ok_apply_M_multi: out[k] = M psi[k] for every right-hand side k; psi [nrhs, ...] complex64."""
+    import torch
+    nrhs = _multi_check(W, psi, "psi", torch.complex64)
+    if out is None:
+        out = torch.empty_like(psi)
+    if _multi_check(W, out, "out", torch.complex64) != nrhs:
+        raise ValueError("out and psi must hold the same number of right-hand sides")
+    st = load().ok_apply_M_multi(W.ptr, int(prec), nrhs, ctypes.c_void_p(psi.data_ptr()),
+                                 ctypes.c_void_p(out.data_ptr()), _stream(stream))
+    _check(st, "ok_apply_M_multi")
+    return out
+
+
+def bicgstab_multi(W: WHandle, src, x=None, tol=1e-10, maxiter=20000, mode=SOLVE_AUTO, delta=1e-3, max_restarts=5,
+                   check_every=8, stream=None, raise_on_noconv=True):
+    """ok_bicgstab_multi: solve M x[k] = src[k] for all right-hand sides (complex128, [nrhs, ...]).
+    Returns (x, list of info dicts)."""
+    import torch
+    nrhs = _multi_check(W, src, "src", torch.complex128)
+    if x is None:
+        x = torch.zeros_like(src)
+    if _multi_check(W, x, "x", torch.complex128) != nrhs:
+        raise ValueError("x and src must hold the same number of right-hand sides")
+    prm = ok_solve_params(float(tol), int(maxiter), int(mode), float(delta), int(max_restarts), int(check_every))
+    infos = (ok_solve_info * nrhs)()
+    st = load().ok_bicgstab_multi(W.ptr, nrhs, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                  ctypes.byref(prm), infos, _stream(stream))
+    out = []
+    for info in infos:
+        d = {k: getattr(info, k) for k, _ in ok_solve_info._fields_}
+        d["status"] = st
+        out.append(d)
+    if st != 0 and (raise_on_noconv or st not in (OK_ENOCONV, OK_EBREAKDOWN)):
+        raise OKError(st, "ok_bicgstab_multi")
+    return x, out
+
+
+def autotune(W: WHandle, prec=F32, nrhs=1, stream=None):
+    """ok_autotune: time the candidate launch shapes and keep the fastest in the handle.
+    Returns (choice, microseconds per launch of the winner)."""
+    choice = ctypes.c_int(0)
+    us = ctypes.c_double(0.0)
+    st = load().ok_autotune(W.ptr, int(prec), int(nrhs), ctypes.byref(choice), ctypes.byref(us), _stream(stream))
+    _check(st, "ok_autotune")
+    return int(choice.value), float(us.value)
+
+
+def set_launch_shape(W: WHandle, prec=F32, staged=0, nr=0, blocks_x=0):
+    """ok_set_launch_shape: pin the launch shapes of the FP32 or FP16-W application."""
+    _check(load().ok_set_launch_shape(W.ptr, int(prec), int(staged), int(nr), int(blocks_x)), "ok_set_launch_shape")
 
 
 def true_residual(W: WHandle, b, x, stream=None) -> float:

@@ -3,6 +3,10 @@
 // (one complex double or two complex floats).  Every kernel first reads the solver's halt flag
 // so that iterations enqueued after convergence are no-ops; scalars (alpha, omega, beta) are read
 // from the device-resident state, so no host round trip is needed between kernels.
+//
+// The three iteration kernels (update_s, update_xr, update_p) also run batched over several
+// right-hand sides: grid row blockIdx.y works on vectors offset by blockIdx.y * n with state
+// st[blockIdx.y] and its own reduction partials (one launch for all systems of a multi-RHS solve).
 #include "ok_launch.cuh"
 
 namespace okgb {
@@ -33,6 +37,8 @@ __global__ void __launch_bounds__(BLAS_THREADS) update_s_kernel(const typename U
                                                                 const typename Unit<R>::T* __restrict__ v,
                                                                 typename Unit<R>::T* __restrict__ s, long long nu,
                                                                 const SolverState* __restrict__ st) {
+  const long long off = (long long)blockIdx.y * nu;
+  r += off; v += off; s += off; st += blockIdx.y;
   if (st->halt) return;
   using U = Unit<R>;
   const cx<R> al = scal<R>(st->alpha);
@@ -55,7 +61,11 @@ __global__ void __launch_bounds__(BLAS_THREADS) update_xr_kernel(typename Unit<R
                                                                  typename Unit<R>::T* __restrict__ r,
                                                                  const typename Unit<R>::T* __restrict__ rhat,
                                                                  long long nu, SolverState* __restrict__ st,
-                                                                 RedArgs ra) {
+                                                                 RedArgs ra, long long pstride) {
+  const long long off = (long long)blockIdx.y * nu;
+  x += off; p += off; s += off; t += off; r += off; rhat += off; st += blockIdx.y;
+  ra.st = st;
+  ra.part += (long long)blockIdx.y * pstride;
   if (st->halt) return;
   using U = Unit<R>;
   const cx<R> al = scal<R>(st->alpha), om = scal<R>(st->omega);
@@ -91,6 +101,8 @@ __global__ void __launch_bounds__(BLAS_THREADS) update_p_kernel(typename Unit<R>
                                                                 const typename Unit<R>::T* __restrict__ r,
                                                                 const typename Unit<R>::T* __restrict__ v,
                                                                 long long nu, const SolverState* __restrict__ st) {
+  const long long off = (long long)blockIdx.y * nu;
+  p += off; r += off; v += off; st += blockIdx.y;
   if (st->halt) return;
   using U = Unit<R>;
   const cx<R> be = scal<R>(st->beta), om = scal<R>(st->omega);
@@ -230,7 +242,7 @@ int launch_update_xr(cx<R>* x, const cx<R>* p, const cx<R>* s, const cx<R>* t, c
   {
     TraceScope ts(sizeof(R) == 8 ? "update_xr_f64" : "update_xr_f32", strm);
     update_xr_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r,
-                                                                  (const T*)rhat, nu, st, ra);
+                                                                  (const T*)rhat, nu, st, ra, 0);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
@@ -256,6 +268,48 @@ int launch_restart(const cx<R>* r, cx<R>* rhat, cx<R>* p, long long n, SolverSta
   {
     TraceScope ts(sizeof(R) == 8 ? "restart_f64" : "restart_f32", strm);
     restart_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((const T*)r, (T*)rhat, (T*)p, nu, st, ra);
+  }
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+// Batched over nrhs systems (vectors [nrhs][n], states [nrhs]); reductions use part + k * pstride
+// for system k, pstride >= 3 * blas_blocks(n / units).
+int launch_update_s_multi(const cx<float>* r, const cx<float>* v, cx<float>* s, long long n, int nrhs, const SolverState* st,
+                          cudaStream_t strm) {
+  using T = Unit<float>::T;
+  const long long nu = units_of<float>(n);
+  {
+    TraceScope ts("update_s_multi", strm);
+    update_s_kernel<float><<<dim3(blas_blocks(nu), nrhs), BLAS_THREADS, 0, strm>>>((const T*)r, (const T*)v, (T*)s, nu, st);
+  }
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+int launch_update_xr_multi(cx<float>* x, const cx<float>* p, const cx<float>* s, const cx<float>* t, cx<float>* r,
+                           const cx<float>* rhat, long long n, int nrhs, SolverState* st, double* part, long long pstride,
+                           cudaStream_t strm) {
+  using T = Unit<float>::T;
+  const long long nu = units_of<float>(n);
+  if (pstride < 3LL * blas_blocks(nu)) return OK_EINVAL;
+  RedArgs ra{st, part, nullptr, FIN_XR};
+  {
+    TraceScope ts("update_xr_multi", strm);
+    update_xr_kernel<float><<<dim3(blas_blocks(nu), nrhs), BLAS_THREADS, 0, strm>>>(
+        (T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r, (const T*)rhat, nu, st, ra, pstride);
+  }
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+int launch_update_p_multi(cx<float>* p, const cx<float>* r, const cx<float>* v, long long n, int nrhs, const SolverState* st,
+                          cudaStream_t strm) {
+  using T = Unit<float>::T;
+  const long long nu = units_of<float>(n);
+  {
+    TraceScope ts("update_p_multi", strm);
+    update_p_kernel<float><<<dim3(blas_blocks(nu), nrhs), BLAS_THREADS, 0, strm>>>((T*)p, (const T*)r, (const T*)v, nu, st);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;

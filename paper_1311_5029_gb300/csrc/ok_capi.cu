@@ -15,6 +15,10 @@ static std::atomic<unsigned long long> g_launches{0};
 static thread_local int g_last_cuda_error = 0;
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void adjust_launches(long long n) {
+  if (n >= 0) g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed);
+  else g_launches.fetch_sub((unsigned long long)(-n), std::memory_order_relaxed);
+}
 
 // ---------------------------------------------------------------------------- tracing
 namespace {
@@ -46,6 +50,9 @@ cudaEvent_t take_event() {
 
 TraceScope::TraceScope(const char* n, cudaStream_t s) : name(n), st(s), slot(-1) {
   if (!g_trace_on.load(std::memory_order_relaxed)) return;
+  // Kernels recorded into a CUDA graph are not timed one by one (the graph launch is).
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   std::lock_guard<std::mutex> lk(g_trace_mu);
   TraceRec r{n, take_event(), take_event()};
   if (!r.a || !r.b) return;
@@ -155,6 +162,46 @@ int ok_bicgstab_ex(const ok_W* W, const void* src, void* x, const ok_solve_param
   if (!W || !src || !x || !params) return OK_EINVAL;
   if ((((uintptr_t)src) | ((uintptr_t)x)) & 15) return OK_EINVAL;
   return bicgstab(W, (const cx<double>*)src, (cx<double>*)x, params, info, (cudaStream_t)stream);
+}
+
+int ok_apply_M_multi(const ok_W* W, ok_prec prec, int nrhs, const void* psi, void* out, void* stream) {
+  if (!W || !psi || !out || nrhs < 1 || (prec != OK_F32 && prec != OK_F32_W16)) return OK_EINVAL;
+  const size_t bytes = (size_t)W->g.V * 12 * 8 * nrhs;
+  const char* a = (const char*)psi;
+  const char* b = (const char*)out;
+  if (a < b + bytes && b < a + bytes) return OK_EINVAL;
+  if (((uintptr_t)psi | (uintptr_t)out) & 15) return OK_EINVAL;
+  const bool w16 = prec == OK_F32_W16;
+  if ((w16 && !W->W16) || (!w16 && !W->W32)) return OK_EINVAL;
+  MultiEpi e{};
+  return launch_apply_multi(W, w16, (const cx<float>*)psi, (cx<float>*)out, nrhs, EPI_NONE, e, multi_shape(W, w16, nrhs),
+                            (cudaStream_t)stream);
+}
+
+int ok_bicgstab_multi(const ok_W* W, int nrhs, const void* src, void* x, const ok_solve_params* params, ok_solve_info* info,
+                      void* stream) {
+  if (!W || !src || !x || !params || nrhs < 1) return OK_EINVAL;
+  if ((((uintptr_t)src) | ((uintptr_t)x)) & 15) return OK_EINVAL;
+  const size_t bytes = (size_t)W->g.V * 12 * 16 * nrhs;
+  const char* a = (const char*)src;
+  const char* b = (const char*)x;
+  if (a < b + bytes && b < a + bytes) return OK_EINVAL;
+  return bicgstab_multi(W, nrhs, (const cx<double>*)src, (cx<double>*)x, params, info, (cudaStream_t)stream);
+}
+
+int ok_autotune(ok_W* W, ok_prec prec, int nrhs, int* choice, double* best_us, void* stream) {
+  return autotune(W, prec, nrhs, choice, best_us, (cudaStream_t)stream);
+}
+
+int ok_set_launch_shape(ok_W* W, ok_prec prec, int staged, int nr, int blocks_x) {
+  if (!W || (prec != OK_F32 && prec != OK_F32_W16)) return OK_EINVAL;
+  if ((staged != 0 && staged != 1) || (nr != 0 && nr != 1 && nr != 2 && nr != 4) || blocks_x < 0 || blocks_x > (1 << 20))
+    return OK_EINVAL;
+  const int k = prec == OK_F32_W16 ? 1 : 0;
+  W->tune.staged[k] = staged;
+  W->tune.mr_nr[k] = nr;
+  W->tune.mr_bx[k] = blocks_x;
+  return OK_SUCCESS;
 }
 
 int ok_bicgstab(const ok_W* W, const void* src, void* x, double tol, int maxiter, ok_solve_info* info, void* stream) {

@@ -156,6 +156,8 @@ struct Geom {
 
 // ---------------------------------------------------------------------------- launch helpers
 void count_launch();
+// Kernels executed by replays of a CUDA graph (n > 0) or launched only into a graph capture (n < 0).
+void adjust_launches(long long n);
 unsigned long long launches();
 void set_cuda_error(cudaError_t e);
 
@@ -172,6 +174,15 @@ inline int grid_for(long long n, int threads) { return (int)((n + threads - 1) /
 
 }  // namespace okgb
 
+namespace okgb {
+// Launch shapes chosen by the autotuner (ok_autotune); zero means the built-in default.
+struct Tune {
+  int staged[2];  // single right-hand side, [FP32 W, FP16 W]: 1 = stream the forward W by TMA
+  int mr_nr[2];   // multi right-hand side: right-hand sides per thread (1..4)
+  int mr_bx[2];   // multi right-hand side: blocks per grid row (0 = as many as fit)
+};
+}  // namespace okgb
+
 // The opaque handle.
 struct ok_W {
   okgb::Geom g;
@@ -184,6 +195,7 @@ struct ok_W {
   void* W16;     // cx<__half>[...]: half-precision copy
   size_t bytes;
   int device;
+  mutable okgb::Tune tune;
 };
 
 #define OK_CUDA_TRY(expr)                                  \

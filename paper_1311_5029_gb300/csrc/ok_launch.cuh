@@ -30,6 +30,23 @@ int launch_apply_df(const ok_W* W, const cx<dd>* psi_df, cx<double>* out, int ep
 int launch_apply_w16(const ok_W* W, const cx<float>* psi, cx<float>* out, int epi, const EpiArgs<float>& ep, cudaStream_t st);
 // Bounded device waits that gave up (the kernel's result is then invalid); optionally reset.
 int read_wait_timeouts(unsigned* n, bool reset);
+// Multi right-hand side apply (ok_mrhs.cu): FP32 fields [nrhs][V][12], W32 or W16 (w16).
+struct MultiEpi {
+  const cx<float>* rhat;  // EPI_DOT: [nrhs][V][12]
+  SolverState* st;        // [nrhs]; EPI_DOT / EPI_TS reduce into st[k] (skipped while st[k].halt)
+  double* part;           // partials of system k at part + k * pstride (pstride >= 3 * grid width)
+  long long pstride;
+  int fin;                // FIN_ALPHA (EPI_DOT) or FIN_OMEGA (EPI_TS)
+  int slot;               // ticket index in each state
+};
+struct MultiShape {
+  int nr;        // right-hand sides per thread, 1..4, dividing nrhs
+  int blocks_x;  // blocks per grid row (0: as many as fit on the device)
+};
+int launch_apply_multi(const ok_W* W, bool w16, const cx<float>* psi, cx<float>* out, int nrhs, int epi, const MultiEpi& ep,
+                       const MultiShape& shape, cudaStream_t st);
+int mrhs_blocks_needed(const ok_W* W);  // upper bound of the grid width
+MultiShape multi_shape(const ok_W* W, bool w16, int nrhs);  // tuned or default
 // FP64 complex -> double-float complex (n complex numbers).
 int launch_to_df(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t st);
 
@@ -47,6 +64,14 @@ int launch_restart(const cx<R>* r, cx<R>* rhat, cx<R>* p, long long n, SolverSta
 int launch_demote(const cx<double>* r64, cx<float>* r32, cx<float>* rhat, cx<float>* p, long long n, bool restart,
                   SolverState* st, double* part, cudaStream_t strm);
 int launch_accum_x(cx<double>* x64, cx<float>* x32, long long n, cudaStream_t strm);
+// Batched iteration kernels over nrhs systems (FP32 vectors [nrhs][n], states [nrhs]).
+int launch_update_s_multi(const cx<float>* r, const cx<float>* v, cx<float>* s, long long n, int nrhs, const SolverState* st,
+                          cudaStream_t strm);
+int launch_update_xr_multi(cx<float>* x, const cx<float>* p, const cx<float>* s, const cx<float>* t, cx<float>* r,
+                           const cx<float>* rhat, long long n, int nrhs, SolverState* st, double* part, long long pstride,
+                           cudaStream_t strm);
+int launch_update_p_multi(cx<float>* p, const cx<float>* r, const cx<float>* v, long long n, int nrhs, const SolverState* st,
+                          cudaStream_t strm);
 // <x, x> and <b, b> in FP64 -> FIN_RESID (state bb = <b, b>, aux = the two sums)
 int launch_norms(const cx<double>* x, const cx<double>* b, long long n, SolverState* st, double* part, cudaStream_t strm);
 
@@ -60,5 +85,10 @@ int expand(const ok_W* W, ok_prec prec, int kind, void* out, cudaStream_t st);
 int bicgstab(const ok_W* W, const cx<double>* b, cx<double>* x, const ok_solve_params* prm, ok_solve_info* info,
              cudaStream_t st);
 int true_residual(const ok_W* W, const cx<double>* b, const cx<double>* x, double* relres, cudaStream_t st);
+int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* b, cx<double>* x, const ok_solve_params* prm, ok_solve_info* info,
+                   cudaStream_t st);
+
+// ok_tune.cu
+int autotune(ok_W* W, ok_prec prec, int nrhs, int* choice, double* best_us, cudaStream_t st);
 
 }  // namespace okgb

@@ -22,7 +22,9 @@
 #include "ok_launch.cuh"
 
 #include <chrono>
+#include <cmath>
 #include <cstring>
+#include <vector>
 
 namespace okgb {
 
@@ -262,6 +264,190 @@ int true_residual(const ok_W* W, const cx<double>* bvec, const cx<double>* x, do
   double rr = hs.h->aux[0], bb = hs.h->aux[1];
   *relres = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
   return OK_SUCCESS;
+}
+
+}  // namespace okgb
+
+// ============================================================================ multi right-hand side
+// nrhs systems M x_k = b_k solved together (the spin-colour sources of one propagator): the
+// mixed-precision method above, run in lockstep.  Each iteration is five launches for all
+// systems (the multi-RHS apply with per-system fused reductions, and the batched vector
+// kernels), captured once into a CUDA graph that is replayed check_every iterations at a time.
+// Every system keeps its own device state; a system that halts is skipped by the kernels while
+// the host handles it (reliable update, restart or completion) and the others go on.
+namespace okgb {
+
+int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* x, const ok_solve_params* prm,
+                   ok_solve_info* info, cudaStream_t st) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!W || !bvec || !x || !prm || nrhs < 1 || nrhs > 64) return OK_EINVAL;
+  if (!(prm->tol > 0.0) || prm->maxiter < 1 || prm->max_restarts < 0 || prm->check_every < 1) return OK_EINVAL;
+  if (!(prm->delta > 0.0 && prm->delta < 1.0)) return OK_EINVAL;
+  int mode = prm->mode;
+  if (mode == OK_SOLVE_AUTO) mode = W->W16 ? OK_SOLVE_MIXED16 : OK_SOLVE_MIXED;
+  if (mode != OK_SOLVE_MIXED && mode != OK_SOLVE_MIXED16) return OK_EINVAL;
+  const bool w16 = mode == OK_SOLVE_MIXED16;
+  if ((w16 && !W->W16) || (!w16 && !W->W32) || !(W->W64 || W->Wdf)) return OK_EINVAL;
+  if ((const void*)bvec == (const void*)x) return OK_EINVAL;
+
+  const long long n = 12LL * W->g.V;
+  const long long N = n * nrhs;
+  Workspace ws;
+  ws.st = st;
+  cudaError_t err = cudaSuccess;
+  long long maxblocks = mrhs_blocks_needed(W);
+  if (blas_blocks(n) > maxblocks) maxblocks = blas_blocks(n);
+  if (blas_blocks(n / 2) > maxblocks) maxblocks = blas_blocks(n / 2);
+  const long long pstride = 4 * maxblocks;
+  double* part = ws.get<double>((size_t)pstride * nrhs, &err);
+  SolverState* dst = ws.get<SolverState>(nrhs, &err);
+  cx<double>* r64 = ws.get<cx<double>>(n, &err);
+  cx<dd>* xdf = W->W64 ? nullptr : ws.get<cx<dd>>(n, &err);
+  IterBufs<float> b{};
+  b.x = ws.get<cx<float>>(N, &err); b.r = ws.get<cx<float>>(N, &err); b.rhat = ws.get<cx<float>>(N, &err);
+  b.p = ws.get<cx<float>>(N, &err); b.v = ws.get<cx<float>>(N, &err); b.s = ws.get<cx<float>>(N, &err);
+  b.t = ws.get<cx<float>>(N, &err);
+  SolverState* h = nullptr;
+  if (cudaMallocHost((void**)&h, sizeof(SolverState) * nrhs) != cudaSuccess) h = nullptr;
+  struct HostFree { SolverState* p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{h};
+  if (!part || !dst || !r64 || (!W->W64 && !xdf) || !b.x || !b.r || !b.rhat || !b.p || !b.v || !b.s || !b.t || !h) {
+    if (err != cudaSuccess) set_cuda_error(err);
+    return OK_ENOMEM;
+  }
+  std::memset(h, 0, sizeof(SolverState) * nrhs);
+  for (int k = 0; k < nrhs; ++k) {
+    h[k].tol2 = prm->tol * prm->tol;
+    h[k].delta2 = prm->delta * prm->delta;
+    h[k].maxiter = prm->maxiter;
+  }
+  OK_CUDA_TRY(cudaMemcpyAsync(dst, h, sizeof(SolverState) * nrhs, cudaMemcpyHostToDevice, st));
+  OK_CUDA_TRY(cudaMemsetAsync(b.x, 0, N * sizeof(cx<float>), st));
+
+  std::vector<ok_solve_info> inf(nrhs);
+  std::vector<int> status(nrhs, 1);  // 1 running, else the final return code (0 = converged)
+  std::vector<double> rr_true(nrhs, 0.0);
+  for (auto& i : inf) std::memset(&i, 0, sizeof(i));
+  const int halt_done = HALT_CONVERGED;
+  auto freeze = [&](int k) {  // keep system k out of further iterations
+    return cudaMemcpyAsync(&dst[k].halt, &halt_done, sizeof(int), cudaMemcpyHostToDevice, st);
+  };
+  auto vec = [&](auto* base, int k) { return base + (size_t)k * n; };
+
+  // Initial residuals, one system at a time (FP64), demoted into the FP32 iteration vectors.
+  for (int k = 0; k < nrhs; ++k) {
+    OK_TRY(launch_norms(vec(x, k), vec(bvec, k), n, &dst[k], part, st));
+    OK_TRY(read_state(&dst[k], &h[k], st));
+    const cx<double>* r0 = vec(bvec, k);
+    if (h[k].aux[0] != 0.0) {
+      OK_TRY(residual64(W, vec(bvec, k), vec(x, k), r64, &dst[k], part, xdf, st));
+      inf[k].fp64_applies++;
+      r0 = r64;
+    }
+    OK_TRY(launch_demote(r0, vec(b.r, k), vec(b.rhat, k), vec(b.p, k), n, true, &dst[k], part, st));
+  }
+  OK_CUDA_TRY(cudaMemcpyAsync(h, dst, sizeof(SolverState) * nrhs, cudaMemcpyDeviceToHost, st));
+  OK_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int k = 0; k < nrhs; ++k) {
+    rr_true[k] = h[k].aux[0];
+    if (h[k].halt == HALT_NONFINITE) status[k] = OK_ENONFINITE;
+    else if (h[k].bb == 0.0) {  // b = 0: x = 0
+      OK_CUDA_TRY(cudaMemsetAsync(vec(x, k), 0, n * sizeof(cx<double>), st));
+      status[k] = OK_SUCCESS;
+      rr_true[k] = 0.0;
+    } else if (h[k].rr < h[k].tol2 * h[k].bb) status[k] = OK_SUCCESS;
+    if (status[k] != 1) OK_CUDA_TRY(freeze(k));
+  }
+
+  const MultiShape shape = multi_shape(W, w16, nrhs);
+  auto iterate_all = [&]() -> int {
+    MultiEpi e1{b.rhat, dst, part, pstride, FIN_ALPHA, 0};
+    OK_TRY(launch_apply_multi(W, w16, b.p, b.v, nrhs, EPI_DOT, e1, shape, st));
+    OK_TRY(launch_update_s_multi(b.r, b.v, b.s, n, nrhs, dst, st));
+    MultiEpi e2{nullptr, dst, part, pstride, FIN_OMEGA, 1};
+    OK_TRY(launch_apply_multi(W, w16, b.s, b.t, nrhs, EPI_TS, e2, shape, st));
+    OK_TRY(launch_update_xr_multi(b.x, b.p, b.s, b.t, b.r, b.rhat, n, nrhs, dst, part, pstride, st));
+    OK_TRY(launch_update_p_multi(b.p, b.r, b.v, n, nrhs, dst, st));
+    return OK_SUCCESS;
+  };
+
+  // The first block of iterations runs with direct launches (it also initialises every kernel's
+  // launch configuration); the same block is then captured once and replayed.
+  cudaGraphExec_t exec = nullptr;
+  struct GraphFree { cudaGraphExec_t* e; ~GraphFree() { if (*e) cudaGraphExecDestroy(*e); } } gf{&exec};
+  long long graph_kernels = 0;
+  bool first = true;
+  int rc_final = OK_SUCCESS;
+  for (;;) {
+    bool running = false;
+    for (int k = 0; k < nrhs; ++k) running = running || status[k] == 1;
+    if (!running) break;
+    if (first || !exec) {
+      for (int it = 0; it < prm->check_every; ++it) OK_TRY(iterate_all());
+    } else {
+      TraceScope ts("bicgstab_multi_graph", st);
+      OK_CUDA_TRY(cudaGraphLaunch(exec, st));
+      adjust_launches(graph_kernels);
+    }
+    if (first) {
+      first = false;
+      cudaGraph_t graph = nullptr;
+      const unsigned long long before = launches();
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        int rc = OK_SUCCESS;
+        for (int it = 0; it < prm->check_every && rc == OK_SUCCESS; ++it) rc = iterate_all();
+        const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        graph_kernels = (long long)(launches() - before);
+        adjust_launches(-graph_kernels);  // captured, not executed
+        if (rc != OK_SUCCESS || ce != cudaSuccess || !graph ||
+            cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+          exec = nullptr;  // replay unavailable: keep launching directly
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+      }
+    }
+    OK_CUDA_TRY(cudaMemcpyAsync(h, dst, sizeof(SolverState) * nrhs, cudaMemcpyDeviceToHost, st));
+    OK_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int k = 0; k < nrhs; ++k) {
+      if (status[k] != 1) continue;
+      const int halt = h[k].halt;
+      if (halt == HALT_NONE) continue;
+      if (halt == HALT_NONFINITE) { status[k] = OK_ENONFINITE; continue; }
+      // fold the FP32 increment into x and recompute the true residual in FP64
+      OK_TRY(launch_accum_x(vec(x, k), vec(b.x, k), n, st));
+      OK_TRY(residual64(W, vec(bvec, k), vec(x, k), r64, &dst[k], part, xdf, st));
+      inf[k].fp64_applies++;
+      OK_TRY(read_state(&dst[k], &h[k], st));
+      rr_true[k] = h[k].aux[0];
+      if (!std::isfinite(rr_true[k])) { status[k] = OK_ENONFINITE; OK_CUDA_TRY(freeze(k)); continue; }
+      if (rr_true[k] < h[k].tol2 * h[k].bb) { status[k] = OK_SUCCESS; OK_CUDA_TRY(freeze(k)); continue; }
+      if (halt == HALT_MAXITER || h[k].iter >= prm->maxiter) { status[k] = OK_ENOCONV; OK_CUDA_TRY(freeze(k)); continue; }
+      if (halt == HALT_UPDATE) {
+        inf[k].reliable_updates++;
+        OK_TRY(launch_demote(r64, vec(b.r, k), vec(b.rhat, k), vec(b.p, k), n, false, &dst[k], part, st));
+        OK_TRY(launch_update_p<float>(vec(b.p, k), vec(b.r, k), vec(b.v, k), n, &dst[k], st));
+        continue;
+      }
+      if (inf[k].restarts >= prm->max_restarts) {
+        status[k] = halt == HALT_BREAKDOWN ? OK_EBREAKDOWN : OK_ENOCONV;
+        OK_CUDA_TRY(freeze(k));
+        continue;
+      }
+      inf[k].restarts++;
+      OK_TRY(launch_demote(r64, vec(b.r, k), vec(b.rhat, k), vec(b.p, k), n, true, &dst[k], part, st));
+    }
+  }
+  OK_CUDA_TRY(cudaMemcpyAsync(h, dst, sizeof(SolverState) * nrhs, cudaMemcpyDeviceToHost, st));
+  OK_CUDA_TRY(cudaStreamSynchronize(st));
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int k = 0; k < nrhs; ++k) {
+    inf[k].true_relres = h[k].bb > 0.0 ? sqrt(rr_true[k] / h[k].bb) : sqrt(rr_true[k]);
+    inf[k].iter_relres = h[k].bb > 0.0 ? sqrt(h[k].rr / h[k].bb) : sqrt(h[k].rr);
+    inf[k].iters = h[k].iter;
+    inf[k].time_ms = ms;
+    if (info) info[k] = inf[k];
+    if (status[k] != OK_SUCCESS && rc_final == OK_SUCCESS) rc_final = status[k];
+  }
+  return rc_final;
 }
 
 }  // namespace okgb
