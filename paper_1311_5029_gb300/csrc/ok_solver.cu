@@ -290,6 +290,35 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
   if ((w16 && !W->W16) || (!w16 && !W->W32) || !(W->W64 || W->Wdf)) return OK_EINVAL;
   if ((const void*)bvec == (const void*)x) return OK_EINVAL;
 
+  // The solve runs on a private non-blocking stream ordered after the caller's stream (a CUDA
+  // graph cannot be captured from the legacy default stream); on every return the caller's stream
+  // is made to wait for it, after the workspace has been released on it.
+  struct OwnStream {
+    cudaStream_t user = nullptr, own = nullptr;
+    ~OwnStream() {
+      if (!own) return;
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(e, own);
+        cudaStreamWaitEvent(user, e, 0);
+        cudaEventDestroy(e);
+      } else {
+        cudaStreamSynchronize(own);
+      }
+      cudaStreamDestroy(own);
+    }
+  } os;
+  os.user = st;
+  {
+    OK_CUDA_TRY(cudaStreamCreateWithFlags(&os.own, cudaStreamNonBlocking));
+    cudaEvent_t e = nullptr;
+    OK_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaError_t e1 = cudaEventRecord(e, st);
+    cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(os.own, e, 0) : e1;
+    cudaEventDestroy(e);
+    OK_CUDA_TRY(e2);
+    st = os.own;
+  }
   const long long n = 12LL * W->g.V;
   const long long N = n * nrhs;
   Workspace ws;
@@ -392,7 +421,9 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
       first = false;
       cudaGraph_t graph = nullptr;
       const unsigned long long before = launches();
-      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();  // no replay: keep launching directly
+      } else {
         int rc = OK_SUCCESS;
         for (int it = 0; it < prm->check_every && rc == OK_SUCCESS; ++it) rc = iterate_all();
         const cudaError_t ce = cudaStreamEndCapture(st, &graph);
