@@ -15,8 +15,11 @@ Action Conjugate Gradient Inverter", PoS LATTICE2013, arXiv:1311.5029, that it f
                 shifted_W_last, the backward ones from Eqs. conjugate and opp_diag_pre_mat, and the
                 operator applied in the form of Eq. minFlopForm (and, as a cross-check, Eq. FinalForm).
 * bicgstab.py -- "O3": textbook BiCGStab (van der Vorst 1992), the paper's bi-stabilized CG.
+* precond.py -- the learned right preconditioner that the library adds to the paper's solver: a
+                gauge-covariant linear network of covariant shifts (the hopping transport of
+                Eq. minFlopForm) and learned spin matrices, with its adjoint and its loss gradient.
 
 Everything is complex128 / float64 numpy arithmetic over whole lattice arrays; there is no
 blocking, fusion or reordering beyond the definitions.
 """
-from . import spin, lattice, gauge, direct, wform, bicgstab  # noqa: F401
+from . import spin, lattice, gauge, direct, wform, bicgstab, precond  # noqa: F401
