@@ -63,6 +63,7 @@ typedef enum { OK_F64 = 0, OK_F32 = 1, OK_F32_W16 = 2 } ok_prec;
 #define OK_W_F32 2
 #define OK_W_DF64 4
 #define OK_W_F16 8   /* half-precision copy (relative rounding 2^-11) for the low-precision iteration */
+#define OK_W_LINKS 16 /* also keep an FP32 copy of the links (for the learned preconditioner, ok_net_*) */
 
 /* Coefficients of the tree-level, tadpole-improved OK action (Sec. 1; they enter the W formulas,
  * Eqs. shifted_W_first .. shifted_W_last).  u0 <= 0: u0 is computed from the mean plaquette of
@@ -97,6 +98,7 @@ typedef struct {
 } ok_solve_params;
 
 typedef struct ok_W ok_W;  /* opaque, library-owned precalculation-matrix set */
+typedef struct ok_net ok_net;  /* opaque, library-owned learned preconditioner (see ok_net_create) */
 
 /* ------------------------------------------------------------------ entry points */
 
@@ -105,7 +107,8 @@ typedef struct ok_W ok_W;  /* opaque, library-owned precalculation-matrix set */
  * and the forward set W^0_x, W^+_{mu,x}, W^{++}_{ii,x}, W^{++}_{ij,x}, W^{+-}_{ij,x} (i < j) per
  * site, unshifted, in a private site-blocked layout.  The backward matrices are not stored: they
  * follow from the forward ones by Eqs. conjugate and opp_diag_pre_mat.  Arithmetic is FP64;
- * W_precs selects the stored copies (OK_W_F64 and/or OK_W_F32).
+ * W_precs selects the stored copies (at least one of OK_W_F64, OK_W_F32, OK_W_DF64, OK_W_F16),
+ * plus OK_W_LINKS to keep an FP32 copy of the links in the handle.
  *   links: device [T][Z][Y][X][4][3][3] complex in links_prec; not retained after the call.
  *   W_out: receives a new handle owned by the caller, released with ok_free_W.
  * Synchronises `stream` before returning (u0 is read back).  Errors: OK_EINVAL (null pointer,
@@ -181,6 +184,45 @@ int ok_bicgstab_multi(const ok_W* W, int nrhs, const void* src, void* x, const o
  * the same handle.  OK_EINVAL for bad arguments or a missing copy, OK_ECUDA.  The paper has no
  * counterpart. */
 int ok_autotune(ok_W* W, ok_prec prec, int nrhs, int* choice, double* best_us, void* stream);
+
+/* Learned right preconditioner (an addition to the paper's unpreconditioned solver, Sec. 2.3).
+ * P = L_K ... L_1 with gauge-covariant linear layers
+ *   (L psi)(x) = sum_d A_d (T_d psi)(x),  d in {0, +x, -x, +y, -y, +z, -z, +t, -t},
+ * T_0 = 1, (T_{+mu} psi)(x) = U_mu(x) psi(x + mu), (T_{-mu} psi)(x) = U_mu(x - mu)^dag psi(x - mu)
+ * (the link transport of the hopping terms of Eq. minFlopForm, with the boundary sign of the
+ * handle's bc) and A_d learned 4 x 4 complex spin matrices shared by all sites.  P is linear in
+ * the source and gauge covariant; the links come from a handle made with OK_W_LINKS.
+ *
+ * Weights are host arrays of layers * 288 doubles: complex128 [layers][9 offsets][4][4] as
+ * (re, im) pairs, offsets in the order above.  The network keeps FP32 weights, Adam moments and a
+ * workspace of (layers + 2) V 96 bytes, allocated at first use; one network must not be used from
+ * two streams at once.
+ *
+ * ok_net_create: layers 1..16, weights NULL for the identity (A_0 = 1).  ok_net_free releases it.
+ * ok_net_apply: out = P psi; psi, out: device [V][4][3] complex64, not overlapping.
+ * ok_net_loss_grad: loss = |P b - x|^2 / |x|^2 for one pair (b, x: device complex64 fields) and,
+ *   if grad is not NULL, its gradient (d/dRe + i d/dIm) into grad (host, layers * 288 doubles).
+ *   Synchronises `stream`.
+ * ok_net_train_step: one Adam step (lr, beta 0.9 / 0.999) on the mean loss of nb pairs
+ *   (b, x: device [nb][V][4][3] complex64); *loss receives the mean loss before the step.
+ *   Synchronises `stream`.
+ * ok_bicgstab_net: ok_bicgstab_ex with the FP32 iteration preconditioned on the right by P
+ *   (BiCGStab on M P y = b, x = x0 + P y); modes OK_SOLVE_MIXED or OK_SOLVE_MIXED16 only, the
+ *   true FP64 residual of x judges convergence as without P.
+ * Errors: OK_EINVAL (null or misaligned pointers, overlap, a handle without OK_W_LINKS, another
+ * device, non-finite weights), OK_ENOMEM, OK_ECUDA; ok_bicgstab_net as ok_bicgstab_ex. */
+int ok_net_create(int layers, const double* weights, ok_net** net);
+void ok_net_free(ok_net* net);
+int ok_net_layers(const ok_net* net);
+int ok_net_get_weights(ok_net* net, double* weights);
+int ok_net_set_weights(ok_net* net, const double* weights);
+int ok_net_apply(ok_net* net, const ok_W* W, const void* psi, void* out, void* stream);
+int ok_net_loss_grad(ok_net* net, const ok_W* W, const void* b, const void* x, double* loss, double* grad,
+                     void* stream);
+int ok_net_train_step(ok_net* net, const ok_W* W, int nb, const void* b, const void* x, double lr,
+                      double* loss, void* stream);
+int ok_bicgstab_net(const ok_W* W, ok_net* net, const void* src, void* x, const ok_solve_params* params,
+                    ok_solve_info* info, void* stream);
 
 /* Pin the launch shapes of the FP32 (OK_F32) or FP16-W (OK_F32_W16) application by hand instead
  * of measuring them: staged (0 or 1) for one right-hand side, nr (0 = default, else 1, 2 or 4

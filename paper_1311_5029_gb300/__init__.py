@@ -21,12 +21,12 @@ from .build import LIB, build as build_library
 
 __all__ = [
     "load", "precompute_W", "apply_M", "bicgstab", "true_residual", "W_expand", "launch_count",
-    "strerror", "OKError", "WHandle", "F64", "F32", "F32_W16", "W_F64", "W_F32", "W_DF64", "W_F16",
+    "strerror", "OKError", "WHandle", "F64", "F32", "F32_W16", "W_F64", "W_F32", "W_DF64", "W_F16", "W_LINKS", "Net", "net_create", "net_apply", "net_loss_grad", "net_train_step", "bicgstab_net",
     "SOLVE_AUTO", "SOLVE_F64", "SOLVE_MIXED", "SOLVE_MIXED16", "header_functions", "wait_timeouts", "apply_M_multi", "bicgstab_multi", "autotune", "set_launch_shape", "trace_enable", "trace_read", "trace_reset", "true_residual_static",
 ]
 
 F64, F32, F32_W16 = 0, 1, 2
-W_F64, W_F32, W_DF64, W_F16 = 1, 2, 4, 8
+W_F64, W_F32, W_DF64, W_F16, W_LINKS = 1, 2, 4, 8, 16
 SOLVE_AUTO, SOLVE_F64, SOLVE_MIXED, SOLVE_MIXED16 = 0, 1, 2, 3
 OK_ENOCONV, OK_EBREAKDOWN = -4, -5
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ok.h")
@@ -96,6 +96,15 @@ def load(path: str | None = None):
         "ok_bicgstab_multi": (i, [vp, i, vp, vp, ctypes.POINTER(ok_solve_params), ctypes.POINTER(ok_solve_info), vp]),
         "ok_autotune": (i, [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]),
         "ok_set_launch_shape": (i, [vp, i, i, i, i]),
+        "ok_net_create": (i, [i, vp, ctypes.POINTER(vp)]),
+        "ok_net_free": (None, [vp]),
+        "ok_net_layers": (i, [vp]),
+        "ok_net_get_weights": (i, [vp, vp]),
+        "ok_net_set_weights": (i, [vp, vp]),
+        "ok_net_apply": (i, [vp, vp, vp, vp, vp]),
+        "ok_net_loss_grad": (i, [vp, vp, vp, vp, ctypes.POINTER(d), vp, vp]),
+        "ok_net_train_step": (i, [vp, vp, i, vp, vp, d, ctypes.POINTER(d), vp]),
+        "ok_bicgstab_net": (i, [vp, vp, vp, vp, ctypes.POINTER(ok_solve_params), ctypes.POINTER(ok_solve_info), vp]),
         "ok_trace_enable": (None, [i]),
         "ok_trace_read": (i, [ctypes.POINTER(ok_trace_stat), i, ctypes.POINTER(i)]),
         "ok_trace_reset": (None, []),
@@ -347,6 +356,122 @@ def autotune(W: WHandle, prec=F32, nrhs=1, stream=None):
 def set_launch_shape(W: WHandle, prec=F32, staged=0, nr=0, blocks_x=0):
     """ok_set_launch_shape: pin the launch shapes of the FP32 or FP16-W application."""
     _check(load().ok_set_launch_shape(W.ptr, int(prec), int(staged), int(nr), int(blocks_x)), "ok_set_launch_shape")
+
+
+class Net:
+    """Learned right preconditioner (gauge-covariant linear layers), owned by the library."""
+
+    def __init__(self, layers: int = 4, weights=None):
+        import numpy as np
+        ptr = ctypes.c_void_p(0)
+        buf = None
+        if weights is not None:
+            w = np.ascontiguousarray(weights, dtype=np.complex128)
+            if w.shape != (layers, 9, 4, 4):
+                raise ValueError("weights must be complex [layers, 9, 4, 4]")
+            buf = w.view(np.float64)
+        arg = ctypes.c_void_p(buf.ctypes.data) if buf is not None else None
+        _check(load().ok_net_create(int(layers), arg, ctypes.byref(ptr)), "ok_net_create")
+        self._ptr = ptr
+        self.layers = int(layers)
+
+    @property
+    def ptr(self):
+        return self._ptr
+
+    @property
+    def weights(self):
+        import numpy as np
+        w = np.zeros((self.layers, 9, 4, 4), dtype=np.complex128)
+        _check(load().ok_net_get_weights(self._ptr, ctypes.c_void_p(w.ctypes.data)), "ok_net_get_weights")
+        return w
+
+    @weights.setter
+    def weights(self, value):
+        import numpy as np
+        w = np.ascontiguousarray(value, dtype=np.complex128)
+        if w.shape != (self.layers, 9, 4, 4):
+            raise ValueError("weights must be complex [layers, 9, 4, 4]")
+        _check(load().ok_net_set_weights(self._ptr, ctypes.c_void_p(w.ctypes.data)), "ok_net_set_weights")
+
+    def free(self):
+        if self._ptr is not None and self._ptr.value:
+            load().ok_net_free(self._ptr)
+            self._ptr = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def net_create(layers: int = 4, weights=None) -> Net:
+    """ok_net_create: a preconditioner network (identity when weights is None)."""
+    return Net(layers, weights)
+
+
+def net_apply(net: Net, W: WHandle, psi, out=None, stream=None):
+    """ok_net_apply: out = P psi (complex64 fields)."""
+    import torch
+    _field_check(W, psi, "psi")
+    if psi.dtype != torch.complex64:
+        raise ValueError("psi must be complex64")
+    if out is None:
+        out = torch.empty_like(psi)
+    _field_check(W, out, "out")
+    _check(load().ok_net_apply(net.ptr, W.ptr, ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                               _stream(stream)), "ok_net_apply")
+    return out
+
+
+def net_loss_grad(net: Net, W: WHandle, b, x, stream=None):
+    """ok_net_loss_grad: (loss, complex gradient [layers, 9, 4, 4]) for one (source, solution) pair."""
+    import numpy as np
+    import torch
+    for t, n in ((b, "b"), (x, "x")):
+        _field_check(W, t, n)
+        if t.dtype != torch.complex64:
+            raise ValueError(f"{n} must be complex64")
+    loss = ctypes.c_double(0.0)
+    g = np.zeros((net.layers, 9, 4, 4), dtype=np.complex128)
+    _check(load().ok_net_loss_grad(net.ptr, W.ptr, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                   ctypes.byref(loss), ctypes.c_void_p(g.ctypes.data), _stream(stream)),
+           "ok_net_loss_grad")
+    return float(loss.value), g
+
+
+def net_train_step(net: Net, W: WHandle, b, x, lr=1e-3, stream=None) -> float:
+    """ok_net_train_step: one Adam step on the pairs b[k], x[k] (complex64 [nb, ...]); returns the mean loss."""
+    import torch
+    nb = _multi_check(W, b, "b", torch.complex64)
+    if _multi_check(W, x, "x", torch.complex64) != nb:
+        raise ValueError("b and x must hold the same number of fields")
+    loss = ctypes.c_double(0.0)
+    _check(load().ok_net_train_step(net.ptr, W.ptr, nb, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                    float(lr), ctypes.byref(loss), _stream(stream)), "ok_net_train_step")
+    return float(loss.value)
+
+
+def bicgstab_net(W: WHandle, net: Net, src, x=None, tol=1e-10, maxiter=20000, mode=SOLVE_MIXED, delta=1e-3,
+                 max_restarts=5, check_every=4, stream=None, raise_on_noconv=True):
+    """ok_bicgstab_net: the mixed-precision solve with the FP32 iteration right-preconditioned by net."""
+    import torch
+    _field_check(W, src, "src")
+    if src.dtype != torch.complex128:
+        raise ValueError("src must be complex128")
+    if x is None:
+        x = torch.zeros_like(src)
+    _field_check(W, x, "x")
+    prm = ok_solve_params(float(tol), int(maxiter), int(mode), float(delta), int(max_restarts), int(check_every))
+    info = ok_solve_info()
+    st = load().ok_bicgstab_net(W.ptr, net.ptr, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                ctypes.byref(prm), ctypes.byref(info), _stream(stream))
+    d = {k: getattr(info, k) for k, _ in ok_solve_info._fields_}
+    d["status"] = st
+    if st != 0 and (raise_on_noconv or st not in (OK_ENOCONV, OK_EBREAKDOWN)):
+        raise OKError(st, "ok_bicgstab_net")
+    return x, d
 
 
 def true_residual(W: WHandle, b, x, stream=None) -> float:

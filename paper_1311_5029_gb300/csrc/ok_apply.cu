@@ -761,7 +761,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB
       // backward warps, which would otherwise wait at the barrier for the longer forward half.
       if (EPI != EPI_NONE) {
         H6<R> ev;
-        load_half<R>(EPI == EPI_DOT ? ep.rhat : EPI == EPI_RESID ? ep.b : psi, s, pr.p, ev);
+        load_half<R>(EPI == EPI_DOT ? ep.rhat : EPI == EPI_RESID ? ep.b : (ep.rhat ? ep.rhat : psi), s, pr.p, ev);
 #pragma unroll
         for (int qq = 0; qq < 2; ++qq)
 #pragma unroll

@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(BLAS_THREADS) update_s_kernel(const typename U
   }
 }
 
-// x += alpha p + omega s;  r = s - omega t;  sums <rhat, r>, <r, r>  ->  FIN_XR
+// x += alpha p + omega s;  r = s - omega t;  sums <rhat, r>, <r, r>  ->  FIN_XR.  With sx set (right
+// preconditioning: p and sx are the preconditioned directions P p and P s) x += alpha p + omega sx.
 template <typename R>
 __global__ void __launch_bounds__(BLAS_THREADS) update_xr_kernel(typename Unit<R>::T* __restrict__ x,
                                                                  const typename Unit<R>::T* __restrict__ p,
@@ -61,9 +62,11 @@ __global__ void __launch_bounds__(BLAS_THREADS) update_xr_kernel(typename Unit<R
                                                                  typename Unit<R>::T* __restrict__ r,
                                                                  const typename Unit<R>::T* __restrict__ rhat,
                                                                  long long nu, SolverState* __restrict__ st,
-                                                                 RedArgs ra, long long pstride) {
+                                                                 RedArgs ra, long long pstride,
+                                                                 const typename Unit<R>::T* __restrict__ sx) {
   const long long off = (long long)blockIdx.y * nu;
   x += off; p += off; s += off; t += off; r += off; rhat += off; st += blockIdx.y;
+  if (sx) sx += off;
   ra.st = st;
   ra.part += (long long)blockIdx.y * pstride;
   if (st->halt) return;
@@ -71,17 +74,18 @@ __global__ void __launch_bounds__(BLAS_THREADS) update_xr_kernel(typename Unit<R
   const cx<R> al = scal<R>(st->alpha), om = scal<R>(st->omega);
   double red[3] = {0.0, 0.0, 0.0};
   OK_GRID_STRIDE(i, nu) {
-    cx<R> xv[U::NC], pv[U::NC], sv[U::NC], tv[U::NC], hv[U::NC];
+    cx<R> xv[U::NC], pv[U::NC], sv[U::NC], tv[U::NC], hv[U::NC], zv[U::NC];
     U::get(x[i], xv);
     U::get(p[i], pv);
     U::get(s[i], sv);
     U::get(t[i], tv);
     U::get(rhat[i], hv);
+    if (sx) U::get(sx[i], zv);
     cx<R> d = mk<R>(0, 0);
     R n2 = 0;
 #pragma unroll
     for (int k = 0; k < U::NC; ++k) {
-      xv[k] = xv[k] + al * pv[k] + om * sv[k];
+      xv[k] = xv[k] + al * pv[k] + om * (sx ? zv[k] : sv[k]);
       sv[k] = sv[k] - om * tv[k];
       d = fma_cj(hv[k], sv[k], d);
       n2 += sv[k].re * sv[k].re + sv[k].im * sv[k].im;
@@ -235,14 +239,14 @@ int launch_update_s(const cx<R>* r, const cx<R>* v, cx<R>* s, long long n, const
 
 template <typename R>
 int launch_update_xr(cx<R>* x, const cx<R>* p, const cx<R>* s, const cx<R>* t, cx<R>* r, const cx<R>* rhat, long long n,
-                     SolverState* st, double* part, cudaStream_t strm) {
+                     SolverState* st, double* part, cudaStream_t strm, const cx<R>* sx) {
   using T = typename Unit<R>::T;
   long long nu = units_of<R>(n);
   RedArgs ra{st, part, nullptr, FIN_XR};
   {
     TraceScope ts(sizeof(R) == 8 ? "update_xr_f64" : "update_xr_f32", strm);
     update_xr_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r,
-                                                                  (const T*)rhat, nu, st, ra, 0);
+                                                                  (const T*)rhat, nu, st, ra, 0, (const T*)sx);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
@@ -297,7 +301,7 @@ int launch_update_xr_multi(cx<float>* x, const cx<float>* p, const cx<float>* s,
   {
     TraceScope ts("update_xr_multi", strm);
     update_xr_kernel<float><<<dim3(blas_blocks(nu), nrhs), BLAS_THREADS, 0, strm>>>(
-        (T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r, (const T*)rhat, nu, st, ra, pstride);
+        (T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r, (const T*)rhat, nu, st, ra, pstride, nullptr);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
@@ -365,8 +369,8 @@ int launch_norms(const cx<double>* x, const cx<double>* b, long long n, SolverSt
 
 template int launch_update_s<double>(const cx<double>*, const cx<double>*, cx<double>*, long long, const SolverState*, cudaStream_t);
 template int launch_update_s<float>(const cx<float>*, const cx<float>*, cx<float>*, long long, const SolverState*, cudaStream_t);
-template int launch_update_xr<double>(cx<double>*, const cx<double>*, const cx<double>*, const cx<double>*, cx<double>*, const cx<double>*, long long, SolverState*, double*, cudaStream_t);
-template int launch_update_xr<float>(cx<float>*, const cx<float>*, const cx<float>*, const cx<float>*, cx<float>*, const cx<float>*, long long, SolverState*, double*, cudaStream_t);
+template int launch_update_xr<double>(cx<double>*, const cx<double>*, const cx<double>*, const cx<double>*, cx<double>*, const cx<double>*, long long, SolverState*, double*, cudaStream_t, const cx<double>*);
+template int launch_update_xr<float>(cx<float>*, const cx<float>*, const cx<float>*, const cx<float>*, cx<float>*, const cx<float>*, long long, SolverState*, double*, cudaStream_t, const cx<float>*);
 template int launch_update_p<double>(cx<double>*, const cx<double>*, const cx<double>*, long long, const SolverState*, cudaStream_t);
 template int launch_update_p<float>(cx<float>*, const cx<float>*, const cx<float>*, long long, const SolverState*, cudaStream_t);
 template int launch_restart<double>(const cx<double>*, cx<double>*, cx<double>*, long long, SolverState*, double*, cudaStream_t);

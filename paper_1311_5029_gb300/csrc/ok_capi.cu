@@ -94,6 +94,7 @@ void ok_free_W(ok_W* W) {
   if (W->W32) cudaFree(W->W32);
   if (W->Wdf) cudaFree(W->Wdf);
   if (W->W16) cudaFree(W->W16);
+  if (W->L32) cudaFree(W->L32);
   delete W;
 }
 
@@ -191,6 +192,52 @@ int ok_bicgstab_multi(const ok_W* W, int nrhs, const void* src, void* x, const o
 
 int ok_autotune(ok_W* W, ok_prec prec, int nrhs, int* choice, double* best_us, void* stream) {
   return autotune(W, prec, nrhs, choice, best_us, (cudaStream_t)stream);
+}
+
+int ok_net_create(int layers, const double* weights, ok_net** net) { return net_create(layers, weights, net); }
+
+void ok_net_free(ok_net* net) { net_free(net); }
+
+int ok_net_layers(const ok_net* net) { return net_layers(net); }
+
+int ok_net_get_weights(ok_net* net, double* weights) {
+  if (!net || !weights) return OK_EINVAL;
+  return net_weights(net, weights, nullptr);
+}
+
+int ok_net_set_weights(ok_net* net, const double* weights) {
+  if (!net || !weights) return OK_EINVAL;
+  return net_weights(net, nullptr, weights);
+}
+
+static bool net_fields_ok(const ok_W* W, const void* a, const void* b, size_t count) {
+  if (!W || !a || !b || (((uintptr_t)a | (uintptr_t)b) & 15)) return false;
+  const size_t bytes = (size_t)W->g.V * 12 * 8 * count;
+  const char* p = (const char*)a;
+  const char* q = (const char*)b;
+  return !(p < q + bytes && q < p + bytes);
+}
+
+int ok_net_apply(ok_net* net, const ok_W* W, const void* psi, void* out, void* stream) {
+  if (!net || !net_fields_ok(W, psi, out, 1)) return OK_EINVAL;
+  return net_apply(net, W, (const cx<float>*)psi, (cx<float>*)out, (cudaStream_t)stream);
+}
+
+int ok_net_loss_grad(ok_net* net, const ok_W* W, const void* b, const void* x, double* loss, double* grad, void* stream) {
+  if (!net || !W || !b || !x || ((((uintptr_t)b) | ((uintptr_t)x)) & 15)) return OK_EINVAL;
+  return net_loss_grad(net, W, (const cx<float>*)b, (const cx<float>*)x, loss, grad, (cudaStream_t)stream);
+}
+
+int ok_net_train_step(ok_net* net, const ok_W* W, int nb, const void* b, const void* x, double lr, double* loss, void* stream) {
+  if (!net || !W || !b || !x || nb < 1 || ((((uintptr_t)b) | ((uintptr_t)x)) & 15)) return OK_EINVAL;
+  return net_train_step(net, W, nb, (const cx<float>*)b, (const cx<float>*)x, lr, loss, (cudaStream_t)stream);
+}
+
+int ok_bicgstab_net(const ok_W* W, ok_net* net, const void* src, void* x, const ok_solve_params* params, ok_solve_info* info,
+                    void* stream) {
+  if (!W || !net || !src || !x || !params) return OK_EINVAL;
+  if ((((uintptr_t)src) | ((uintptr_t)x)) & 15) return OK_EINVAL;
+  return bicgstab_net(W, net, (const cx<double>*)src, (cx<double>*)x, params, info, (cudaStream_t)stream);
 }
 
 int ok_set_launch_shape(ok_W* W, ok_prec prec, int staged, int nr, int blocks_x) {

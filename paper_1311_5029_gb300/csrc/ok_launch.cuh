@@ -14,7 +14,7 @@ enum : int {
 };
 
 template <typename R> struct EpiArgs {
-  const cx<R>* rhat;   // EPI_DOT
+  const cx<R>* rhat;   // EPI_DOT; EPI_TS (split kernel): if set, the y of <out, y> instead of psi
   const cx<R>* b;      // EPI_RESID
   RedArgs ra;
   unsigned* ticket;
@@ -56,7 +56,7 @@ template <typename R>
 int launch_update_s(const cx<R>* r, const cx<R>* v, cx<R>* s, long long n, const SolverState* st, cudaStream_t strm);
 template <typename R>
 int launch_update_xr(cx<R>* x, const cx<R>* p, const cx<R>* s, const cx<R>* t, cx<R>* r, const cx<R>* rhat, long long n,
-                     SolverState* st, double* part, cudaStream_t strm);
+                     SolverState* st, double* part, cudaStream_t strm, const cx<R>* sx = nullptr);
 template <typename R>
 int launch_update_p(cx<R>* p, const cx<R>* r, const cx<R>* v, long long n, const SolverState* st, cudaStream_t strm);
 template <typename R>
@@ -87,6 +87,18 @@ int bicgstab(const ok_W* W, const cx<double>* b, cx<double>* x, const ok_solve_p
 int true_residual(const ok_W* W, const cx<double>* b, const cx<double>* x, double* relres, cudaStream_t st);
 int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* b, cx<double>* x, const ok_solve_params* prm, ok_solve_info* info,
                    cudaStream_t st);
+
+// ok_net.cu (learned right preconditioner)
+int net_create(int layers, const double* w, ok_net** out);
+void net_free(ok_net* N);
+int net_weights(ok_net* N, double* get, const double* set);
+int net_layers(const ok_net* N);
+int net_apply(ok_net* N, const ok_W* W, const cx<float>* in, cx<float>* out, cudaStream_t st);
+int net_loss_grad(ok_net* N, const ok_W* W, const cx<float>* b, const cx<float>* x, double* loss, double* grad, cudaStream_t st);
+int net_train_step(ok_net* N, const ok_W* W, int nb, const cx<float>* b, const cx<float>* x, double lr, double* loss,
+                   cudaStream_t st);
+int bicgstab_net(const ok_W* W, ok_net* net, const cx<double>* b, cx<double>* x, const ok_solve_params* prm,
+                 ok_solve_info* info, cudaStream_t st);
 
 // ok_tune.cu
 int autotune(ok_W* W, ok_prec prec, int nrhs, int* choice, double* best_us, cudaStream_t st);

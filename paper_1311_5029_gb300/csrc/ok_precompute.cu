@@ -507,11 +507,19 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
   return OK_SUCCESS;
 }
 
+// FP64 links -> FP32 copy kept in the handle (OK_W_LINKS).
+__global__ void links_to_f32_kernel(const cx<double>* __restrict__ in, cx<float>* __restrict__ out, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = mk<float>((float)in[i].re, (float)in[i].im);
+}
+
 int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, const ok_coeffs* c,
                int precs, cudaStream_t st, ok_W** W_out) {
   if (!lat || !links || !c || !W_out) return OK_EINVAL;
   if (links_prec != OK_F64 && links_prec != OK_F32) return OK_EINVAL;
-  if (precs <= 0 || (precs & ~(OK_W_F64 | OK_W_F32 | OK_W_DF64 | OK_W_F16))) return OK_EINVAL;
+  if ((precs & (OK_W_F64 | OK_W_F32 | OK_W_DF64 | OK_W_F16)) == 0 ||
+      (precs & ~(OK_W_F64 | OK_W_F32 | OK_W_DF64 | OK_W_F16 | OK_W_LINKS)))
+    return OK_EINVAL;
   if (!(c->u0 > 0.0) && c->u0 > 0.0) return OK_EINVAL;
   *W_out = nullptr;
   Geom g;
@@ -535,6 +543,7 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
     if (W->W32) cudaFree(W->W32);
     if (W->Wdf) cudaFree(W->Wdf);
     if (W->W16) cudaFree(W->W16);
+    if (W->L32) cudaFree(W->L32);
     delete W;
     return code;
   };
@@ -563,8 +572,24 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
     e = cudaMemsetAsync(W->W16, 0, elems * sizeof(cx<__half>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
   }
+  const size_t nlink = (size_t)g.V * 4 * 9;
+  if (precs & OK_W_LINKS) {
+    e = cudaMalloc(&W->L32, nlink * sizeof(cx<float>));
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
+    if (links_prec == OK_F32) {
+      e = cudaMemcpyAsync(W->L32, links, nlink * sizeof(cx<float>), cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
+    } else {
+      links_to_f32_kernel<<<grid_for((long long)nlink, 256), 256, 0, st>>>((const cx<double>*)links, (cx<float>*)W->L32,
+                                                                            (long long)nlink);
+      count_launch();
+      e = cudaGetLastError();
+      if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
+    }
+  }
   W->bytes = (W->W64 ? elems * sizeof(cx<double>) : 0) + (W->W32 ? elems * sizeof(cx<float>) : 0) +
-             (W->Wdf ? elems * sizeof(cx<dd>) : 0) + (W->W16 ? elems * sizeof(cx<__half>) : 0);
+             (W->Wdf ? elems * sizeof(cx<dd>) : 0) + (W->W16 ? elems * sizeof(cx<__half>) : 0) +
+             (W->L32 ? nlink * sizeof(cx<float>) : 0);
   int nb1 = grid_for(g.V, K1_THREADS);
   e = cudaMalloc(&EB, (size_t)g.V * 6 * 9 * sizeof(cx<double>));
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }

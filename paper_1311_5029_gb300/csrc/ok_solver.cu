@@ -86,14 +86,41 @@ int apply_iter(const ok_W* W, const cx<R>* psi, cx<R>* out, int epi, const EpiAr
   return launch_apply<R>(W, psi, out, epi, ep, st);
 }
 
+// Right preconditioner of the FP32 iteration (null: none) and its two direction buffers.
+struct Precond {
+  ok_net* net = nullptr;
+  cx<float>* zp = nullptr;  // P p
+  cx<float>* zs = nullptr;  // P s
+};
+
+// One BiCGStab iteration.  With a right preconditioner P the operator is M P:  v = M (P p),
+// t = M (P s) with <t, s> taken against the unpreconditioned s, and the solution increment is
+// alpha P p + omega P s, so x stays in the original variables.
 template <typename R>
-int iterate(const ok_W* W, const IterBufs<R>& b, long long n, SolverState* dst, double* part, bool w16, cudaStream_t st) {
+int iterate(const ok_W* W, const IterBufs<R>& b, long long n, SolverState* dst, double* part, bool w16, const Precond& pc,
+            cudaStream_t st) {
+  const cx<R>* pin = b.p;
+  const cx<R>* sin = b.s;
+  bool pre = false;
+  if constexpr (sizeof(R) == 4) {
+    if (pc.net) {
+      pre = true;
+      OK_TRY(net_apply(pc.net, W, b.p, pc.zp, st));
+      pin = pc.zp;
+    }
+  }
   EpiArgs<R> e1{b.rhat, nullptr, RedArgs{dst, part, nullptr, FIN_ALPHA}, &dst->ticket[0], &dst->halt};
-  OK_TRY(apply_iter<R>(W, b.p, b.v, EPI_DOT, e1, w16, st));
+  OK_TRY(apply_iter<R>(W, pin, b.v, EPI_DOT, e1, w16, st));
   OK_TRY(launch_update_s<R>(b.r, b.v, b.s, n, dst, st));
-  EpiArgs<R> e2{nullptr, nullptr, RedArgs{dst, part, nullptr, FIN_OMEGA}, &dst->ticket[1], &dst->halt};
-  OK_TRY(apply_iter<R>(W, b.s, b.t, EPI_TS, e2, w16, st));
-  OK_TRY(launch_update_xr<R>(b.x, b.p, b.s, b.t, b.r, b.rhat, n, dst, part, st));
+  if constexpr (sizeof(R) == 4) {
+    if (pre) {
+      OK_TRY(net_apply(pc.net, W, b.s, pc.zs, st));
+      sin = pc.zs;
+    }
+  }
+  EpiArgs<R> e2{pre ? b.s : nullptr, nullptr, RedArgs{dst, part, nullptr, FIN_OMEGA}, &dst->ticket[1], &dst->halt};
+  OK_TRY(apply_iter<R>(W, sin, b.t, EPI_TS, e2, w16, st));
+  OK_TRY(launch_update_xr<R>(b.x, pin, b.s, b.t, b.r, b.rhat, n, dst, part, st, pre ? sin : nullptr));
   OK_TRY(launch_update_p<R>(b.p, b.r, b.v, n, dst, st));
   return OK_SUCCESS;
 }
@@ -116,8 +143,10 @@ int residual64(const ok_W* W, const cx<double>* bvec, const cx<double>* x, cx<do
 
 }  // namespace
 
-int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solve_params* prm, ok_solve_info* info,
-             cudaStream_t st) {
+namespace {
+
+int bicgstab_impl(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solve_params* prm, ok_solve_info* info,
+                  cudaStream_t st, ok_net* net) {
   auto t0 = std::chrono::steady_clock::now();
   if (!W || !bvec || !x || !prm) return OK_EINVAL;
   if (!(prm->tol > 0.0) || prm->maxiter < 1 || prm->max_restarts < 0 || prm->check_every < 1) return OK_EINVAL;
@@ -136,6 +165,7 @@ int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solv
   if (!has64) return OK_EINVAL;
   if (mode == OK_SOLVE_MIXED && !(prm->delta > 0.0 && prm->delta < 1.0)) return OK_EINVAL;
   if ((const void*)bvec == (const void*)x) return OK_EINVAL;
+  if (net && (mode != OK_SOLVE_MIXED || !W->L32)) return OK_EINVAL;  // the network runs in the FP32 iteration
 
   const long long n = 12LL * W->g.V;
   ok_solve_info inf;
@@ -178,6 +208,13 @@ int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solv
     if (!b32.x || !b32.r || !b32.rhat || !b32.p || !b32.v || !b32.s || !b32.t) { set_cuda_error(err); return OK_ENOMEM; }
     OK_CUDA_TRY(cudaMemsetAsync(b32.x, 0, n * sizeof(cx<float>), st));
   }
+  Precond pc;
+  if (net) {
+    pc.net = net;
+    pc.zp = ws.get<cx<float>>(n, &err);
+    pc.zs = ws.get<cx<float>>(n, &err);
+    if (!pc.zp || !pc.zs) { set_cuda_error(err); return OK_ENOMEM; }
+  }
 
   auto finish = [&](int rc, double rr_true) {
     inf.true_relres = h->bb > 0.0 ? sqrt(rr_true / h->bb) : sqrt(rr_true);
@@ -213,8 +250,8 @@ int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solv
 
   for (;;) {
     for (int k = 0; k < prm->check_every; ++k) {
-      if (mode == OK_SOLVE_F64) OK_TRY(iterate<double>(W, b64, n, dst, part, false, st));
-      else OK_TRY(iterate<float>(W, b32, n, dst, part, w16, st));
+      if (mode == OK_SOLVE_F64) OK_TRY(iterate<double>(W, b64, n, dst, part, false, Precond{}, st));
+      else OK_TRY(iterate<float>(W, b32, n, dst, part, w16, pc, st));
     }
     OK_TRY(read_state(dst, h, st));
     int halt = h->halt;
@@ -244,6 +281,19 @@ int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solv
     if (mode == OK_SOLVE_F64) OK_TRY(launch_restart<double>(r64, b64.rhat, b64.p, n, dst, part, st));
     else OK_TRY(launch_demote(r64, b32.r, b32.rhat, b32.p, n, true, dst, part, st));
   }
+}
+
+}  // namespace
+
+int bicgstab(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok_solve_params* prm, ok_solve_info* info,
+             cudaStream_t st) {
+  return bicgstab_impl(W, bvec, x, prm, info, st, nullptr);
+}
+
+int bicgstab_net(const ok_W* W, ok_net* net, const cx<double>* bvec, cx<double>* x, const ok_solve_params* prm,
+                 ok_solve_info* info, cudaStream_t st) {
+  if (!net) return OK_EINVAL;
+  return bicgstab_impl(W, bvec, x, prm, info, st, net);
 }
 
 int true_residual(const ok_W* W, const cx<double>* bvec, const cx<double>* x, double* relres, cudaStream_t st) {
