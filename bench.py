@@ -184,7 +184,7 @@ def measured_peaks():
 
 def apply_source_hash():
     h = hashlib.sha256()
-    for f in ("ok_apply.cu", "ok_internal.cuh", "ok_reduce.cuh", "ok_launch.cuh"):
+    for f in ("ok_apply.cu", "ok_pair.cuh", "ok_internal.cuh", "ok_reduce.cuh", "ok_launch.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1311_5029_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

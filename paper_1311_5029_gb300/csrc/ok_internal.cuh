@@ -193,7 +193,7 @@ struct ok_W {
   void* W32;     // cx<float>[...]
   void* Wdf;     // cx<dd>[...]: FP64-accurate double-float copy
   void* W16;     // cx<__half>[...]: half-precision copy
-  void* L32;     // cx<float>[V][4][3][3]: FP32 links (OK_W_LINKS), for the preconditioner network
+  void* L32;     // cx<float>[nblk][4][9][32]: FP32 links, site-blocked (OK_W_LINKS), for the preconditioner network
   size_t bytes;
   int device;
   mutable okgb::Tune tune;

@@ -6,7 +6,8 @@
 // BiCGStab on M P y = b (x = P y) keeps a fixed operator; it is gauge covariant because only the
 // links move colour.
 //
-// Kernels (FP32 fields, FP32 links from the handle's OK_W_LINKS copy, FP32 weights):
+// Kernels (FP32 fields, FP32 weights, FP32 links from the handle's OK_W_LINKS copy in the
+// site-blocked layout of W):
 //   layer:    one thread per site, the nine offsets unrolled; weights staged in shared memory.
 //             The adjoint layer L^dag = sum_d A_d^dag T_{-d} is the same kernel with the offsets
 //             reversed and the weights conjugate-transposed.
@@ -77,11 +78,13 @@ __device__ __forceinline__ void load_sp(const cx<float>* __restrict__ p, int sit
   }
 }
 
+// U_mu(site) from the site-blocked FP32 link copy (element e of the 32 sites of a block is one
+// contiguous row).
 __device__ __forceinline__ void link(const cx<float>* __restrict__ L, int site, int mu, M3<float>& U) {
-  const float2* q = reinterpret_cast<const float2*>(L) + ((size_t)site * 4 + mu) * 9;
+  const float2* q = reinterpret_cast<const float2*>(L) + ((size_t)(site >> 5) * 4 + mu) * 9 * LANES + (site & 31);
 #pragma unroll
   for (int e = 0; e < 9; ++e) {
-    const float2 d = __ldg(q + e);
+    const float2 d = __ldg(q + e * LANES);
     U.e[e] = mk<float>(d.x, d.y);
   }
 }

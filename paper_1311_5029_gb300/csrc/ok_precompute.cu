@@ -507,10 +507,17 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
   return OK_SUCCESS;
 }
 
-// FP64 links -> FP32 copy kept in the handle (OK_W_LINKS).
-__global__ void links_to_f32_kernel(const cx<double>* __restrict__ in, cx<float>* __restrict__ out, long long n) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = mk<float>((float)in[i].re, (float)in[i].im);
+// Links -> the FP32 copy kept in the handle (OK_W_LINKS), in the site-blocked layout of W:
+// element e of U_mu at the site in lane l of block blk is at ((blk * 4 + mu) * 9 + e) * 32 + l,
+// so a warp over 32 consecutive sites reads each element as one 256-byte row.
+template <typename T>
+__global__ void links_blocked_kernel(const cx<T>* __restrict__ in, cx<float>* __restrict__ out, int V) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;  // (site, mu, e) in input order
+  if (i >= 36LL * V) return;
+  const int site = (int)(i / 36), r = (int)(i % 36);
+  const int mu = r / 9, e = r % 9;
+  const cx<T> u = in[i];
+  out[(((size_t)(site >> 5) * 4 + mu) * 9 + e) * LANES + (site & 31)] = mk<float>((float)u.re, (float)u.im);
 }
 
 int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, const ok_coeffs* c,
@@ -572,20 +579,20 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
     e = cudaMemsetAsync(W->W16, 0, elems * sizeof(cx<__half>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
   }
-  const size_t nlink = (size_t)g.V * 4 * 9;
+  const size_t nlink = (size_t)g.nblk * LANES * 4 * 9;  // blocked: whole 32-site blocks
   if (precs & OK_W_LINKS) {
     e = cudaMalloc(&W->L32, nlink * sizeof(cx<float>));
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
-    if (links_prec == OK_F32) {
-      e = cudaMemcpyAsync(W->L32, links, nlink * sizeof(cx<float>), cudaMemcpyDeviceToDevice, st);
-      if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
-    } else {
-      links_to_f32_kernel<<<grid_for((long long)nlink, 256), 256, 0, st>>>((const cx<double>*)links, (cx<float>*)W->L32,
-                                                                            (long long)nlink);
-      count_launch();
-      e = cudaGetLastError();
-      if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
-    }
+    e = cudaMemsetAsync(W->L32, 0, nlink * sizeof(cx<float>), st);
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
+    const int nbl = grid_for(36LL * g.V, 256);
+    if (links_prec == OK_F32)
+      links_blocked_kernel<float><<<nbl, 256, 0, st>>>((const cx<float>*)links, (cx<float>*)W->L32, g.V);
+    else
+      links_blocked_kernel<double><<<nbl, 256, 0, st>>>((const cx<double>*)links, (cx<float>*)W->L32, g.V);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
   }
   W->bytes = (W->W64 ? elems * sizeof(cx<double>) : 0) + (W->W32 ? elems * sizeof(cx<float>) : 0) +
              (W->Wdf ? elems * sizeof(cx<dd>) : 0) + (W->W16 ? elems * sizeof(cx<__half>) : 0) +
