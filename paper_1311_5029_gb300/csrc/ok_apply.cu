@@ -623,11 +623,25 @@ template <typename WT> struct StagedW {
   }
 };
 
-// Issue the copies of chunk q of this block (tile blockIdx.x + (q / NCHUNK) gridDim.x) into slot
+#ifndef OK_TILE_SWIZZLE
+#define OK_TILE_SWIZZLE 0
+#endif
+// First tile of this block; the block then walks every gridDim.x-th tile.  With OK_TILE_SWIZZLE,
+// on a grid of G = k S blocks (S multiprocessors) the blocks b, b + S, b + 2S, ..., which a full
+// persistent grid places on one SM, take consecutive tiles, so that their neighbour gathers (the
+// rows above and below a tile) can share L1.
+__device__ __forceinline__ int tile_rank(int sms) {
+  const int b = blockIdx.x, G = gridDim.x;
+  if (OK_TILE_SWIZZLE && sms > 0 && G % sms == 0) return (b % sms) * (G / sms) + b / sms;
+  return b;
+}
+
+// Issue the copies of chunk q of this block (tile tile_rank + (q / NCHUNK) gridDim.x) into slot
 // q % OK_STAGES.  Called by one thread.
 template <typename WT>
-__device__ __forceinline__ void issue_chunk(const cx<WT>* __restrict__ W, cx<WT>* stage, unsigned long long* full, int q) {
-  const int tile = blockIdx.x + (q / NCHUNK) * gridDim.x;
+__device__ __forceinline__ void issue_chunk(const cx<WT>* __restrict__ W, cx<WT>* stage, unsigned long long* full, int q,
+                                            int rank) {
+  const int tile = rank + (q / NCHUNK) * gridDim.x;
   const int c = q % NCHUNK, slot = q % OK_STAGES;
   const int m0 = chunk_first(c), n = chunk_count(c);
   constexpr unsigned mbytes = 9 * LANES * sizeof(cx<WT>);
@@ -663,7 +677,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB
   // registers); the block and grid reductions that follow are FP64.
   R red[3] = {0, 0, 0};
   const int ntiles = (g.V + SPLIT_SITES - 1) / SPLIT_SITES;
-  const int nq = (STAGED && (int)blockIdx.x < ntiles) ? ((ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1) * NCHUNK : 0;
+  const int rank = tile_rank(g.sms);
+  const int nq = (STAGED && rank < ntiles) ? ((ntiles - 1 - rank) / (int)gridDim.x + 1) * NCHUNK : 0;
   int qc = 0;  // next chunk (forward warps)
   bool staged_ok = true;
   if constexpr (STAGED) {
@@ -673,7 +688,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB
     }
     __syncthreads();
     if (threadIdx.x == 0)
-      for (int k = 0; k < OK_STAGES && k < nq; ++k) issue_chunk<WT>(W, stage, full, k);
+      for (int k = 0; k < OK_STAGES && k < nq; ++k) issue_chunk<WT>(W, stage, full, k, rank);
   }
   // Wait for chunk qc; the forward warps then read it through a StagedW.
   auto chunk = [&](int m0) {
@@ -684,11 +699,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB
   // Both forward warps are done with chunk qc: its slot takes chunk qc + OK_STAGES.
   auto release = [&]() {
     fwd_bar_sync();
-    if (threadIdx.x == 0 && qc + OK_STAGES < nq) issue_chunk<WT>(W, stage, full, qc + OK_STAGES);
+    if (threadIdx.x == 0 && qc + OK_STAGES < nq) issue_chunk<WT>(W, stage, full, qc + OK_STAGES, rank);
     ++qc;
   };
   int kb = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, kb ^= 1) {
+  for (int tile = rank; tile < ntiles; tile += gridDim.x, kb ^= 1) {
   const int s = tile * SPLIT_SITES + (t >> 1);
   const bool active = s < g.V;
   H6<R> acc;
@@ -859,7 +874,9 @@ static void launch_split(const cx<WT>* W, const cx<R>* psi, cx<R>* out, const Ge
     resident = nb * sm_count();
   }
   const int tiles = grid_for(g.V, SPLIT_SITES);
-  kern<<<tiles < resident ? tiles : resident, SPLIT_THREADS, dyn, st>>>(W, psi, out, g, c0q, a, b, ep);
+  Geom gs = g;
+  gs.sms = sm_count();
+  kern<<<tiles < resident ? tiles : resident, SPLIT_THREADS, dyn, st>>>(W, psi, out, gs, c0q, a, b, ep);
 }
 
 // The split kernel streams the forward W through shared memory by TMA when the handle's tuning

@@ -152,6 +152,7 @@ struct Geom {
   int bcneg;     // bit mu set: antiperiodic in direction mu
   int V;         // number of sites
   int nblk;      // ceil(V / 32)
+  int sms;       // set by persistent launches: multiprocessors of the device (0 = unknown)
 };
 
 // ---------------------------------------------------------------------------- launch helpers
