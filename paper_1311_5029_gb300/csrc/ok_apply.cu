@@ -624,7 +624,7 @@ template <typename WT> struct StagedW {
 };
 
 #ifndef OK_TILE_SWIZZLE
-#define OK_TILE_SWIZZLE 0
+#define OK_TILE_SWIZZLE 1
 #endif
 // First tile of this block; the block then walks every gridDim.x-th tile.  With OK_TILE_SWIZZLE,
 // on a grid of G = k S blocks (S multiprocessors) the blocks b, b + S, b + 2S, ..., which a full

@@ -53,6 +53,17 @@ def spin_colour_sources(dims, site=0):
     return b.reshape((12,) + synth.lattice_shape(dims) + (4, 3))
 
 
+def _gaussian_sources(dims, n, seed):
+    """n Gaussian complex sources (re, im iid N(0, 1)) drawn on the device from a seeded generator;
+    the training pairs need many, and drawing them on the host would dominate the run."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    shape = (n,) + synth.lattice_shape(dims) + (4, 3, 2)
+    r = torch.randn(shape, generator=g, device="cuda", dtype=torch.float64)
+    return torch.view_as_complex(r)
+
+
 def _links(dims, eps, seed):
     import torch
     return torch.from_numpy(synth.random_links(dims, eps, seed)).cuda()
@@ -104,8 +115,7 @@ def form_net(quick=False, layers=4, epochs=6, lr=1e-2):
         bs, xs = [], []
         for j in range(0, per_field, 12):
             n = min(12, per_field - j)
-            b = torch.stack([torch.from_numpy(synth.gaussian_source(dims, 30000 + 1000 * f + j + k)).cuda()
-                             for k in range(n)])
+            b = _gaussian_sources(dims, n, 30000 + 1000 * f + j)
             x, _ = ok.bicgstab_multi(W, b, tol=1e-8, mode=ok.SOLVE_MIXED16, delta=1e-2, check_every=8)
             bs.append(b.to(torch.complex64))
             xs.append(x.to(torch.complex64))
