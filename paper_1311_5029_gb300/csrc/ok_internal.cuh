@@ -153,6 +153,7 @@ struct Geom {
   int V;         // number of sites
   int nblk;      // ceil(V / 32)
   int sms;       // set by persistent launches: multiprocessors of the device (0 = unknown)
+  int S[4];      // site-index strides: 1, X, X Y, X Y Z
 };
 
 // ---------------------------------------------------------------------------- launch helpers

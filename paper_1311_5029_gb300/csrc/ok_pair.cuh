@@ -126,24 +126,29 @@ template <typename R> __device__ __forceinline__ void mdv(cx<R> (&y)[3], const M
 }
 
 // ---------------------------------------------------------------------------- geometry
-// Neighbour x + d with fermion boundary sign; |d_mu| <= 2.
+// Neighbour x + d with fermion boundary sign; |d_mu| <= 2.  The coordinate is wrapped by at most
+// two conditional subtractions (two are needed only when L_mu < |d_mu|, on lattices of extent 1
+// or 2); the sign flips once per wrap across an antiperiodic boundary.
 template <int D0, int D1, int D2, int D3>
 __device__ __forceinline__ int nbr_site(const int (&c)[4], const Geom& g, bool& neg) {
   const int d[4] = {D0, D1, D2, D3};
-  int idx = 0, stride = 1;
+  int idx = 0;
   neg = false;
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
     int x = c[mu];
     if (d[mu] != 0) {
       const int L = g.L[mu];
-      int y = x + d[mu];
-      int q = (y + 2 * L) / L - 2;  // floor(y / L) for y >= -2L
-      x = y - q * L;
-      if ((g.bcneg >> mu) & q & 1) neg = !neg;
+      x += d[mu];
+      int wraps = 0;
+      if (d[mu] > 0) {
+        if (x >= L) { x -= L; wraps = 1; if (x >= L) { x -= L; wraps = 2; } }
+      } else {
+        if (x < 0) { x += L; wraps = 1; if (x < 0) { x += L; wraps = 2; } }
+      }
+      if (((g.bcneg >> mu) & 1) && (wraps & 1)) neg = !neg;
     }
-    idx += x * stride;
-    stride *= g.L[mu];
+    idx += x * g.S[mu];
   }
   return idx;
 }

@@ -474,6 +474,9 @@ static int check_lattice(const ok_lattice* lat, Geom* g) {
   }
   g->V = (int)V;
   g->nblk = (int)((V + LANES - 1) / LANES);
+  g->sms = 0;
+  g->S[0] = 1;
+  for (int mu = 1; mu < 4; ++mu) g->S[mu] = g->S[mu - 1] * g->L[mu - 1];
   return OK_SUCCESS;
 }
 
