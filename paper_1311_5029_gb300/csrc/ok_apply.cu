@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB
   // buffer k & 1 for tile k only after the barrier of tile k - 1, which the forward half passes
   // only after it has read buffer (k - 2) & 1 = k & 1.
   __shared__ cx<R> xch[2][64][6];
-  __shared__ cx<R> xev[EPI == EPI_NONE ? 1 : 2][64][6];
+  __shared__ __align__(16) cx<R> xev[EPI == EPI_NONE ? 1 : 2][64][6];
   __shared__ __align__(8) unsigned long long full[STAGED ? OK_STAGES : 1];
   extern __shared__ __align__(128) unsigned char stage_raw[];
   cx<WT>* stage = reinterpret_cast<cx<WT>*>(stage_raw);
@@ -758,6 +758,18 @@ __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB
       pair_diag<R, 1, 2, 2, true, false>(Wg, psi, c, g, s, pr, acc);
     }
   } else if (active) {
+      // The epilogue's own half-spinor (rhat, b, or the y of <out, y>) is copied into shared memory
+      // asynchronously (cp.async, no registers held) while this half works through its hops.
+      if constexpr (EPI != EPI_NONE) {
+        const cx<R>* src = EPI == EPI_DOT ? ep.rhat : EPI == EPI_RESID ? ep.b : (ep.rhat ? ep.rhat : psi);
+        const char* gsrc = reinterpret_cast<const char*>(src + (size_t)s * 12 + 6 * pr.p);
+        char* dst = reinterpret_cast<char*>(&xev[kb][t][0]);
+#pragma unroll
+        for (int k = 0; k < (int)(6 * sizeof(cx<R>)) / 16; ++k)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst + 16 * k)), "l"(gsrc + 16 * k)
+                       : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      }
       pair_spatial<R, 0, false, true>(Wg, psi, c, g, s, pr, acc);
       pair_spatial<R, 1, false, true>(Wg, psi, c, g, s, pr, acc);
       pair_spatial<R, 2, false, true>(Wg, psi, c, g, s, pr, acc);
@@ -772,16 +784,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB
       for (int qq = 0; qq < 2; ++qq)
 #pragma unroll
         for (int k = 0; k < 3; ++k) xch[kb][t][3 * qq + k] = acc.v[qq][k];
-      // The epilogue's own half-spinor (rhat, psi or b at this site) is fetched here, on the
-      // backward warps, which would otherwise wait at the barrier for the longer forward half.
-      if (EPI != EPI_NONE) {
-        H6<R> ev;
-        load_half<R>(EPI == EPI_DOT ? ep.rhat : EPI == EPI_RESID ? ep.b : (ep.rhat ? ep.rhat : psi), s, pr.p, ev);
-#pragma unroll
-        for (int qq = 0; qq < 2; ++qq)
-#pragma unroll
-          for (int k = 0; k < 3; ++k) xev[kb][t][3 * qq + k] = ev.v[qq][k];
-      }
+      if constexpr (EPI != EPI_NONE) asm volatile("cp.async.wait_all;" ::: "memory");
   }
   __syncthreads();
   if (half == 0 && active) {
