@@ -278,6 +278,14 @@ unsigned long long ok_launch_count(void);
  * OK_ECUDA if the copy fails.  The paper has no counterpart. */
 int ok_wait_timeouts(unsigned* n, int reset);
 
+/* Failure injection for the test of the bounded waits: every later application that streams W
+ * through shared memory (a handle pinned with ok_set_launch_shape(staged = 1)) makes block 0
+ * declare extra_bytes more for its first bulk copy than the copy delivers, so that wait runs out
+ * after about half a second; the launch then ends (its result is invalid), the timeouts are
+ * counted for ok_wait_timeouts and the context stays usable.  extra_bytes = 0 turns it off;
+ * other values must be multiples of 16 up to 65536 (else OK_EINVAL).  Synchronous. */
+int ok_inject_wait_timeout(unsigned extra_bytes);
+
 /* Kernel tracing (per-kernel-class timing with CUDA events recorded on the launching stream).
  * While enabled, every kernel launch of the library is bracketed by two CUDA events; ok_trace_read
  * waits for the recorded events, folds them into per-class totals and returns up to `max` entries

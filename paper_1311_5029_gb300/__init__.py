@@ -92,6 +92,7 @@ def load(path: str | None = None):
         "ok_W_expand": (i, [vp, i, i, vp, vp]),
         "ok_launch_count": (ctypes.c_ulonglong, []),
         "ok_wait_timeouts": (i, [ctypes.POINTER(ctypes.c_uint), i]),
+        "ok_inject_wait_timeout": (i, [ctypes.c_uint]),
         "ok_apply_M_multi": (i, [vp, i, i, vp, vp, vp]),
         "ok_bicgstab_multi": (i, [vp, i, vp, vp, ctypes.POINTER(ok_solve_params), ctypes.POINTER(ok_solve_info), vp]),
         "ok_autotune": (i, [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]),
@@ -140,6 +141,11 @@ def wait_timeouts(reset: bool = False) -> int:
     n = ctypes.c_uint(0)
     _check(load().ok_wait_timeouts(ctypes.byref(n), 1 if reset else 0), "ok_wait_timeouts")
     return int(n.value)
+
+
+def inject_wait_timeout(extra_bytes: int):
+    """ok_inject_wait_timeout: failure injection for the bounded device waits (0 turns it off)."""
+    _check(load().ok_inject_wait_timeout(int(extra_bytes)), "ok_inject_wait_timeout")
 
 
 def trace_enable(on: bool = True):

@@ -561,6 +561,9 @@ template <typename WT> constexpr size_t staged_smem() { return (size_t)OK_STAGES
 // Bounded waits: a wait that has not completed after about 2^30 SM cycles (half a second) gives
 // up, counts itself here and lets the kernel run to its end (the result is then invalid).
 __device__ unsigned g_wait_timeouts;
+// Failure injection for the bounded waits: extra bytes that block 0 declares for its first chunk
+// (which its copies never deliver, so that wait runs out).  0 outside the failure-detection test.
+__device__ unsigned g_stage_test_bytes;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
@@ -579,12 +582,15 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return done != 0;
 }
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+// Waits until phase `parity` of `bar` completes or `limit` SM cycles pass; a wait that runs out
+// is counted in g_wait_timeouts when `count` is set.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit = 1LL << 30,
+                                          bool count = true) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1LL << 30)) {
-      atomicAdd(&g_wait_timeouts, 1u);
+    if (clock64() - t0 > limit) {
+      if (count) atomicAdd(&g_wait_timeouts, 1u);
       return false;
     }
   }
@@ -647,7 +653,8 @@ __device__ __forceinline__ void issue_chunk(const cx<WT>* __restrict__ W, cx<WT>
   constexpr unsigned mbytes = 9 * LANES * sizeof(cx<WT>);
   // The slot was last read through the generic proxy; order those reads before the async writes.
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_expect_tx(&full[slot], n * mbytes);
+  const unsigned extra = (q == 0 && blockIdx.x == 0) ? g_stage_test_bytes : 0u;
+  mbar_expect_tx(&full[slot], n * mbytes + extra);
   for (int j = 0; j < n; ++j)
     bulk_g2s(stage + (size_t)slot * slot_elems<WT>() + (size_t)j * smat_elems<WT>(),
              W + ((size_t)tile * NMAT + m0 + j) * (9 * LANES), mbytes, &full[slot]);
@@ -681,25 +688,41 @@ __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB
   const int nq = (STAGED && rank < ntiles) ? ((ntiles - 1 - rank) / (int)gridDim.x + 1) * NCHUNK : 0;
   int qc = 0;  // next chunk (forward warps)
   bool staged_ok = true;
+  // Failure path: a wait that runs out sets stage_abort; no further chunk is issued, the block
+  // finishes without waiting (its results are invalid and the timeout is counted), and thread 0
+  // waits once more, briefly, for every chunk it issued but did not see arrive, so that no bulk
+  // copy is in flight when the block exits.
+  __shared__ int stage_abort;
+  int issued = 0, unwaited_from = -1;
   if constexpr (STAGED) {
     if (threadIdx.x == 0) {
       for (int k = 0; k < OK_STAGES; ++k) mbar_init(&full[k], 1);
       mbar_fence_init();
+      stage_abort = 0;
     }
     __syncthreads();
     if (threadIdx.x == 0)
-      for (int k = 0; k < OK_STAGES && k < nq; ++k) issue_chunk<WT>(W, stage, full, k, rank);
+      for (; issued < OK_STAGES && issued < nq; ++issued) issue_chunk<WT>(W, stage, full, issued, rank);
   }
   // Wait for chunk qc; the forward warps then read it through a StagedW.
   auto chunk = [&](int m0) {
     const int slot = qc % OK_STAGES;
-    if (staged_ok) staged_ok = mbar_wait(&full[slot], (qc / OK_STAGES) & 1);
+    if (staged_ok) {
+      staged_ok = mbar_wait(&full[slot], (qc / OK_STAGES) & 1);
+      if (!staged_ok) {
+        stage_abort = 1;
+        unwaited_from = qc;
+      }
+    }
     return StagedW<WT>{stage + (size_t)slot * slot_elems<WT>(), m0};
   };
   // Both forward warps are done with chunk qc: its slot takes chunk qc + OK_STAGES.
   auto release = [&]() {
     fwd_bar_sync();
-    if (threadIdx.x == 0 && qc + OK_STAGES < nq) issue_chunk<WT>(W, stage, full, qc + OK_STAGES, rank);
+    if (threadIdx.x == 0 && qc + OK_STAGES < nq && !stage_abort) {
+      issue_chunk<WT>(W, stage, full, qc + OK_STAGES, rank);
+      ++issued;
+    }
     ++qc;
   };
   int kb = 0;
@@ -839,6 +862,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB
     }
   }
   }  // tiles
+  if constexpr (STAGED) {
+    if (threadIdx.x == 0 && unwaited_from >= 0)
+      for (int q = unwaited_from; q < issued; ++q) mbar_wait(&full[q % OK_STAGES], (q / OK_STAGES) & 1, 1LL << 24, false);
+  }
   if (EPI == EPI_DOT || EPI == EPI_RESID) {
     double v2[2] = {(double)red[0], (double)red[1]};
     grid_reduce<2, SPLIT_THREADS>(v2, ep.ra, ep.ticket);
@@ -952,6 +979,13 @@ int launch_apply_w16(const ok_W* Wh, const cx<float>* psi, cx<float>* out, int e
     }
   }
   OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+// Failure injection for the bounded waits (see g_stage_test_bytes).
+int set_stage_test_bytes(unsigned bytes) {
+  if (bytes % 16 != 0 || bytes > (1u << 16)) return OK_EINVAL;
+  if (cudaMemcpyToSymbol(g_stage_test_bytes, &bytes, sizeof(unsigned)) != cudaSuccess) return OK_ECUDA;
   return OK_SUCCESS;
 }
 

@@ -266,6 +266,8 @@ int ok_W_expand(const ok_W* W, ok_prec prec, int kind, void* out, void* stream) 
 
 unsigned long long ok_launch_count(void) { return launches(); }
 
+int ok_inject_wait_timeout(unsigned extra_bytes) { return okgb::set_stage_test_bytes(extra_bytes); }
+
 int ok_wait_timeouts(unsigned* n, int reset) {
   if (!n) return OK_EINVAL;
   return okgb::read_wait_timeouts(n, reset != 0);

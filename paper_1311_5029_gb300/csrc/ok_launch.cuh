@@ -30,6 +30,7 @@ int launch_apply_df(const ok_W* W, const cx<dd>* psi_df, cx<double>* out, int ep
 int launch_apply_w16(const ok_W* W, const cx<float>* psi, cx<float>* out, int epi, const EpiArgs<float>& ep, cudaStream_t st);
 // Bounded device waits that gave up (the kernel's result is then invalid); optionally reset.
 int read_wait_timeouts(unsigned* n, bool reset);
+int set_stage_test_bytes(unsigned bytes);  // failure injection for the bounded waits
 // Multi right-hand side apply (ok_mrhs.cu): FP32 fields [nrhs][V][12], W32 or W16 (w16).
 struct MultiEpi {
   const cx<float>* rhat;  // EPI_DOT: [nrhs][V][12]

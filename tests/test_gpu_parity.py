@@ -217,15 +217,62 @@ def test_double_float_16cube32_sampled():
 
 
 def test_staged_copies_complete():
-    """The FP32 and FP16-W applies stream W through bulk copies and bounded barrier waits; on
-    lattices with ragged last tiles and with many tiles per resident block no wait may give up."""
+    """The TMA-staged split kernel (pinned with ok_set_launch_shape): FP32 and FP16-W applies against
+    the oracle on lattices with ragged last tiles and with many tiles per resident block; no
+    bounded wait may give up."""
     ok.wait_timeouts(reset=True)
     for dims, seed in (((7, 6, 5, 9), 1), ((16, 16, 16, 32), 2), ((3, 5, 4, 3), 3)):
-        U = to_dev(synth.random_links(dims, 0.3, 7100 + seed))
-        W = ok.precompute_W(U, synth.random_coeffs(7200 + seed), (1, 1, 1, 1), ok.W_F32 | ok.W_F16)
-        psi = to_dev(synth.gaussian_source(dims, 7300 + seed).astype(np.complex64))
-        a = ok.apply_M(W, psi)
-        h = ok.apply_M(W, psi, prec=ok.F32_W16)
-        torch.cuda.synchronize()
-        assert torch.isfinite(torch.view_as_real(a)).all() and torch.isfinite(torch.view_as_real(h)).all()
+        U = synth.random_links(dims, 0.3, 7100 + seed)
+        c = synth.random_coeffs(7200 + seed)
+        W = ok.precompute_W(to_dev(U), c, (1, 1, 1, 1), ok.W_F32 | ok.W_F16)
+        ok.set_launch_shape(W, ok.F32, staged=1)
+        ok.set_launch_shape(W, ok.F32_W16, staged=1)
+        psi = synth.gaussian_source(dims, 7300 + seed).astype(np.complex64)
+        a = ok.apply_M(W, to_dev(psi)).cpu().numpy()
+        h = ok.apply_M(W, to_dev(psi), prec=ok.F32_W16).cpu().numpy()
+        V = int(np.prod(dims))
+        if V <= 5000:
+            exp = wform.apply(U, c, psi.astype(np.complex128), (1, 1, 1, 1))
+            assert rel_l2(a, exp) < FP32_TOL
+            assert rel_l2(h, exp) < 4 * 2.0 ** -11
+        else:
+            sites = _sample_sites(V)
+            exp = direct.apply_at(U, c, psi.astype(np.complex128), sites)
+            assert rel_l2(a.reshape(V, 4, 3)[sites], exp) < FP32_TOL
     assert ok.wait_timeouts() == 0
+
+
+def test_staged_mixed_solve():
+    dims, U, c, b = synth.workload_inputs("16^3x32")
+    W = ok.precompute_W(to_dev(U), c, (1, 1, 1, 1), ok.W_F64 | ok.W_F32)
+    ok.set_launch_shape(W, ok.F32, staged=1)
+    x, info = ok.bicgstab(W, to_dev(b), tol=1e-10, mode=ok.SOLVE_MIXED, delta=1e-4)
+    assert info["status"] == 0 and info["true_relres"] < 1e-10
+    Mx = wform.apply_lean(U, c, x.cpu().numpy(), (1, 1, 1, 1))
+    assert np.linalg.norm(b - Mx) / np.linalg.norm(b) < 1e-10
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable():
+    """Failure detection without a fault: block 0 of a staged launch is made to expect 16 bytes
+    that never arrive; its waits give up after about half a second, the launch ends, the timeouts
+    are counted, and the next launches on the same context are correct."""
+    dims = (8, 8, 8, 8)
+    U = synth.random_links(dims, 0.3, 7401)
+    c = synth.placeholder_coeffs(0.5)
+    W = ok.precompute_W(to_dev(U), c, (1, 1, 1, 1), ok.W_F32)
+    ok.set_launch_shape(W, ok.F32, staged=1)
+    psi = to_dev(synth.gaussian_source(dims, 7402).astype(np.complex64))
+    ok.wait_timeouts(reset=True)
+    try:
+        ok.inject_wait_timeout(16)
+        ok.apply_M(W, psi)
+        torch.cuda.synchronize()
+    finally:
+        ok.inject_wait_timeout(0)
+    assert ok.wait_timeouts(reset=True) >= 1
+    got = ok.apply_M(W, psi).cpu().numpy()
+    exp = wform.apply(U, c, psi.cpu().numpy().astype(np.complex128), (1, 1, 1, 1))
+    assert rel_l2(got, exp) < FP32_TOL
+    assert ok.wait_timeouts() == 0
+    with pytest.raises(ok.OKError):
+        ok.inject_wait_timeout(7)
