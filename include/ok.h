@@ -223,6 +223,11 @@ int ok_net_train_step(ok_net* net, const ok_W* W, int nb, const void* b, const v
                       double* loss, void* stream);
 int ok_bicgstab_net(const ok_W* W, ok_net* net, const void* src, void* x, const ok_solve_params* params,
                     ok_solve_info* info, void* stream);
+/* ok_bicgstab_multi with every system's FP32 iteration right-preconditioned by the network (the
+ * network applied to each system in turn; arguments and results as ok_bicgstab_multi, the handle
+ * needs OK_W_LINKS). */
+int ok_bicgstab_multi_net(const ok_W* W, ok_net* net, int nrhs, const void* src, void* x,
+                          const ok_solve_params* params, ok_solve_info* info, void* stream);
 
 /* Pin the launch shapes of the FP32 (OK_F32) or FP16-W (OK_F32_W16) application by hand instead
  * of measuring them: staged (0 or 1) for one right-hand side, nr (0 = default, else 1, 2 or 4

@@ -106,6 +106,7 @@ def load(path: str | None = None):
         "ok_net_loss_grad": (i, [vp, vp, vp, vp, ctypes.POINTER(d), vp, vp]),
         "ok_net_train_step": (i, [vp, vp, i, vp, vp, d, ctypes.POINTER(d), vp]),
         "ok_bicgstab_net": (i, [vp, vp, vp, vp, ctypes.POINTER(ok_solve_params), ctypes.POINTER(ok_solve_info), vp]),
+        "ok_bicgstab_multi_net": (i, [vp, vp, i, vp, vp, ctypes.POINTER(ok_solve_params), ctypes.POINTER(ok_solve_info), vp]),
         "ok_trace_enable": (None, [i]),
         "ok_trace_read": (i, [ctypes.POINTER(ok_trace_stat), i, ctypes.POINTER(i)]),
         "ok_trace_reset": (None, []),
@@ -326,9 +327,9 @@ def apply_M_multi(W: WHandle, psi, out=None, prec=F32, stream=None):
 
 
 def bicgstab_multi(W: WHandle, src, x=None, tol=1e-10, maxiter=20000, mode=SOLVE_AUTO, delta=1e-3, max_restarts=5,
-                   check_every=8, stream=None, raise_on_noconv=True):
-    """ok_bicgstab_multi: solve M x[k] = src[k] for all right-hand sides (complex128, [nrhs, ...]).
-    Returns (x, list of info dicts)."""
+                   check_every=8, stream=None, raise_on_noconv=True, net=None):
+    """ok_bicgstab_multi (ok_bicgstab_multi_net with a preconditioner network): solve M x[k] = src[k]
+    for all right-hand sides (complex128, [nrhs, ...]).  Returns (x, list of info dicts)."""
     import torch
     nrhs = _multi_check(W, src, "src", torch.complex128)
     if x is None:
@@ -337,8 +338,12 @@ def bicgstab_multi(W: WHandle, src, x=None, tol=1e-10, maxiter=20000, mode=SOLVE
         raise ValueError("x and src must hold the same number of right-hand sides")
     prm = ok_solve_params(float(tol), int(maxiter), int(mode), float(delta), int(max_restarts), int(check_every))
     infos = (ok_solve_info * nrhs)()
-    st = load().ok_bicgstab_multi(W.ptr, nrhs, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(x.data_ptr()),
-                                  ctypes.byref(prm), infos, _stream(stream))
+    if net is None:
+        st = load().ok_bicgstab_multi(W.ptr, nrhs, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                      ctypes.byref(prm), infos, _stream(stream))
+    else:
+        st = load().ok_bicgstab_multi_net(W.ptr, net.ptr, nrhs, ctypes.c_void_p(src.data_ptr()),
+                                          ctypes.c_void_p(x.data_ptr()), ctypes.byref(prm), infos, _stream(stream))
     out = []
     for info in infos:
         d = {k: getattr(info, k) for k, _ in ok_solve_info._fields_}

@@ -293,7 +293,7 @@ int launch_update_s_multi(const cx<float>* r, const cx<float>* v, cx<float>* s, 
 
 int launch_update_xr_multi(cx<float>* x, const cx<float>* p, const cx<float>* s, const cx<float>* t, cx<float>* r,
                            const cx<float>* rhat, long long n, int nrhs, SolverState* st, double* part, long long pstride,
-                           cudaStream_t strm) {
+                           cudaStream_t strm, const cx<float>* sx) {
   using T = Unit<float>::T;
   const long long nu = units_of<float>(n);
   if (pstride < 3LL * blas_blocks(nu)) return OK_EINVAL;
@@ -301,7 +301,7 @@ int launch_update_xr_multi(cx<float>* x, const cx<float>* p, const cx<float>* s,
   {
     TraceScope ts("update_xr_multi", strm);
     update_xr_kernel<float><<<dim3(blas_blocks(nu), nrhs), BLAS_THREADS, 0, strm>>>(
-        (T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r, (const T*)rhat, nu, st, ra, pstride, nullptr);
+        (T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r, (const T*)rhat, nu, st, ra, pstride, (const T*)sx);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;

@@ -190,6 +190,17 @@ int ok_bicgstab_multi(const ok_W* W, int nrhs, const void* src, void* x, const o
   return bicgstab_multi(W, nrhs, (const cx<double>*)src, (cx<double>*)x, params, info, (cudaStream_t)stream);
 }
 
+int ok_bicgstab_multi_net(const ok_W* W, ok_net* net, int nrhs, const void* src, void* x, const ok_solve_params* params,
+                          ok_solve_info* info, void* stream) {
+  if (!W || !net || !src || !x || !params || nrhs < 1) return OK_EINVAL;
+  if ((((uintptr_t)src) | ((uintptr_t)x)) & 15) return OK_EINVAL;
+  const size_t bytes = (size_t)W->g.V * 12 * 16 * nrhs;
+  const char* a = (const char*)src;
+  const char* b = (const char*)x;
+  if (a < b + bytes && b < a + bytes) return OK_EINVAL;
+  return bicgstab_multi(W, nrhs, (const cx<double>*)src, (cx<double>*)x, params, info, (cudaStream_t)stream, net);
+}
+
 int ok_autotune(ok_W* W, ok_prec prec, int nrhs, int* choice, double* best_us, void* stream) {
   return autotune(W, prec, nrhs, choice, best_us, (cudaStream_t)stream);
 }

@@ -33,7 +33,7 @@ int read_wait_timeouts(unsigned* n, bool reset);
 int set_stage_test_bytes(unsigned bytes);  // failure injection for the bounded waits
 // Multi right-hand side apply (ok_mrhs.cu): FP32 fields [nrhs][V][12], W32 or W16 (w16).
 struct MultiEpi {
-  const cx<float>* rhat;  // EPI_DOT: [nrhs][V][12]
+  const cx<float>* rhat;  // EPI_DOT: [nrhs][V][12]; EPI_TS: if set, the y of <out, y> instead of psi
   SolverState* st;        // [nrhs]; EPI_DOT / EPI_TS reduce into st[k] (skipped while st[k].halt)
   double* part;           // partials of system k at part + k * pstride (pstride >= 3 * grid width)
   long long pstride;
@@ -70,7 +70,7 @@ int launch_update_s_multi(const cx<float>* r, const cx<float>* v, cx<float>* s, 
                           cudaStream_t strm);
 int launch_update_xr_multi(cx<float>* x, const cx<float>* p, const cx<float>* s, const cx<float>* t, cx<float>* r,
                            const cx<float>* rhat, long long n, int nrhs, SolverState* st, double* part, long long pstride,
-                           cudaStream_t strm);
+                           cudaStream_t strm, const cx<float>* sx = nullptr);
 int launch_update_p_multi(cx<float>* p, const cx<float>* r, const cx<float>* v, long long n, int nrhs, const SolverState* st,
                           cudaStream_t strm);
 // <x, x> and <b, b> in FP64 -> FIN_RESID (state bb = <b, b>, aux = the two sums)
@@ -87,7 +87,7 @@ int bicgstab(const ok_W* W, const cx<double>* b, cx<double>* x, const ok_solve_p
              cudaStream_t st);
 int true_residual(const ok_W* W, const cx<double>* b, const cx<double>* x, double* relres, cudaStream_t st);
 int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* b, cx<double>* x, const ok_solve_params* prm, ok_solve_info* info,
-                   cudaStream_t st);
+                   cudaStream_t st, ok_net* net = nullptr);
 
 // ok_net.cu (learned right preconditioner)
 int net_create(int layers, const double* w, ok_net** out);

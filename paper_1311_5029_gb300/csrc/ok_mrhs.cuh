@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(MR_THREADS, mr_minb<NR>())
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
             H6<R> ev;
-            load_half<R>(EPI == EPI_DOT ? ep.rhat + (r0 + r) * rs : P + r * rs, s, pr.p, ev);
+            load_half<R>((EPI == EPI_DOT || ep.rhat) ? ep.rhat + (r0 + r) * rs : P + r * rs, s, pr.p, ev);
 #pragma unroll
             for (int q = 0; q < 2; ++q)
 #pragma unroll

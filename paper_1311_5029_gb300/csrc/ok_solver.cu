@@ -328,7 +328,7 @@ int true_residual(const ok_W* W, const cx<double>* bvec, const cx<double>* x, do
 namespace okgb {
 
 int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* x, const ok_solve_params* prm,
-                   ok_solve_info* info, cudaStream_t st) {
+                   ok_solve_info* info, cudaStream_t st, ok_net* net) {
   auto t0 = std::chrono::steady_clock::now();
   if (!W || !bvec || !x || !prm || nrhs < 1 || nrhs > 64) return OK_EINVAL;
   if (!(prm->tol > 0.0) || prm->maxiter < 1 || prm->max_restarts < 0 || prm->check_every < 1) return OK_EINVAL;
@@ -339,6 +339,7 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
   const bool w16 = mode == OK_SOLVE_MIXED16;
   if ((w16 && !W->W16) || (!w16 && !W->W32) || !(W->W64 || W->Wdf)) return OK_EINVAL;
   if ((const void*)bvec == (const void*)x) return OK_EINVAL;
+  if (net && !W->L32) return OK_EINVAL;  // the network needs the handle's FP32 links
 
   // The solve runs on a private non-blocking stream ordered after the caller's stream (a CUDA
   // graph cannot be captured from the legacy default stream); on every return the caller's stream
@@ -386,6 +387,9 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
   b.x = ws.get<cx<float>>(N, &err); b.r = ws.get<cx<float>>(N, &err); b.rhat = ws.get<cx<float>>(N, &err);
   b.p = ws.get<cx<float>>(N, &err); b.v = ws.get<cx<float>>(N, &err); b.s = ws.get<cx<float>>(N, &err);
   b.t = ws.get<cx<float>>(N, &err);
+  cx<float>* zp = net ? ws.get<cx<float>>(N, &err) : nullptr;  // P p and P s of every system
+  cx<float>* zs = net ? ws.get<cx<float>>(N, &err) : nullptr;
+  if (net && (!zp || !zs)) { set_cuda_error(err); return OK_ENOMEM; }
   SolverState* h = nullptr;
   if (cudaMallocHost((void**)&h, sizeof(SolverState) * nrhs) != cudaSuccess) h = nullptr;
   struct HostFree { SolverState* p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{h};
@@ -438,13 +442,25 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
   }
 
   const MultiShape shape = multi_shape(W, w16, nrhs);
+  // One iteration for every system; with a right preconditioner P (applied to each system in
+  // turn) the operator is M P, as in iterate() above.
   auto iterate_all = [&]() -> int {
+    const cx<float>* pin = b.p;
+    const cx<float>* sin = b.s;
+    if (net) {
+      for (int k = 0; k < nrhs; ++k) OK_TRY(net_apply(net, W, vec(b.p, k), vec(zp, k), st));
+      pin = zp;
+    }
     MultiEpi e1{b.rhat, dst, part, pstride, FIN_ALPHA, 0};
-    OK_TRY(launch_apply_multi(W, w16, b.p, b.v, nrhs, EPI_DOT, e1, shape, st));
+    OK_TRY(launch_apply_multi(W, w16, pin, b.v, nrhs, EPI_DOT, e1, shape, st));
     OK_TRY(launch_update_s_multi(b.r, b.v, b.s, n, nrhs, dst, st));
-    MultiEpi e2{nullptr, dst, part, pstride, FIN_OMEGA, 1};
-    OK_TRY(launch_apply_multi(W, w16, b.s, b.t, nrhs, EPI_TS, e2, shape, st));
-    OK_TRY(launch_update_xr_multi(b.x, b.p, b.s, b.t, b.r, b.rhat, n, nrhs, dst, part, pstride, st));
+    if (net) {
+      for (int k = 0; k < nrhs; ++k) OK_TRY(net_apply(net, W, vec(b.s, k), vec(zs, k), st));
+      sin = zs;
+    }
+    MultiEpi e2{net ? b.s : nullptr, dst, part, pstride, FIN_OMEGA, 1};
+    OK_TRY(launch_apply_multi(W, w16, sin, b.t, nrhs, EPI_TS, e2, shape, st));
+    OK_TRY(launch_update_xr_multi(b.x, pin, b.s, b.t, b.r, b.rhat, n, nrhs, dst, part, pstride, st, net ? sin : nullptr));
     OK_TRY(launch_update_p_multi(b.p, b.r, b.v, n, nrhs, dst, st));
     return OK_SUCCESS;
   };

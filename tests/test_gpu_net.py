@@ -125,3 +125,42 @@ def test_net_argument_errors():
         net.weights = bad
     with pytest.raises(ok.OKError):
         ok.precompute_W(U, c, (1, 1, 1, 1), ok.W_LINKS)   # links alone: no W copy
+
+
+def test_multi_rhs_solve_with_the_network():
+    """The multi-RHS solve right-preconditioned by the network: the identity network changes
+    nothing, a trained one cuts the iterations, and every system reaches 1e-10 (oracle apply)."""
+    dims, bc = (8, 8, 8, 8), (1, 1, 1, 1)
+    c = synth.placeholder_coeffs(0.5)
+    U = synth.random_links(dims, 0.2, 9601)
+    W = ok.precompute_W(to_dev(U), c, bc, ok.W_F64 | ok.W_F32 | ok.W_F16 | ok.W_LINKS)
+    V = int(np.prod(dims))
+    b = torch.zeros((12, V, 12), dtype=torch.complex128, device="cuda")
+    for k in range(12):
+        b[k, 5, k] = 1.0
+    b = b.reshape((12,) + synth.lattice_shape(dims) + (4, 3))
+    x0, i0 = ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED16, delta=1e-2)
+    x1, i1 = ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED16, delta=1e-2, net=ok.Net(2))
+    assert [i["iters"] for i in i0] == [i["iters"] for i in i1]
+    # a network trained on Gaussian pairs of two other fields
+    net = ok.Net(4)
+    pairs = []
+    for f in range(2):
+        Uf = synth.random_links(dims, 0.15 + 0.1 * f, 9610 + f)
+        Wf = ok.precompute_W(to_dev(Uf), c, bc, ok.W_F64 | ok.W_F32 | ok.W_LINKS)
+        bs = torch.stack([to_dev(synth.gaussian_source(dims, 9620 + 12 * f + k)) for k in range(12)])
+        xs, _ = ok.bicgstab_multi(Wf, bs, tol=1e-8, mode=ok.SOLVE_MIXED, delta=1e-2)
+        pairs.append((Wf, bs.to(torch.complex64), xs.to(torch.complex64)))
+    for step in range(120):
+        Wf, bs, xs = pairs[step % 2]
+        j = 4 * ((step // 2) % 3)
+        ok.net_train_step(net, Wf, bs[j:j + 4], xs[j:j + 4], lr=1e-2 if step < 80 else 3e-3)
+    x2, i2 = ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED16, delta=1e-2, net=net)
+    assert max(i["iters"] for i in i2) < min(i["iters"] for i in i0), ([i["iters"] for i in i2], [i["iters"] for i in i0])
+    xs2, bs = x2.cpu().numpy(), b.cpu().numpy()
+    for k in (0, 6, 11):
+        r = np.linalg.norm(bs[k] - wform.apply(U, c, xs2[k], bc)) / np.linalg.norm(bs[k])
+        assert i2[k]["true_relres"] < 1e-10 and r < 1e-10, (k, r)
+    with pytest.raises(ok.OKError):            # the handle needs the links copy
+        W2 = ok.precompute_W(to_dev(U), c, bc, ok.W_F64 | ok.W_F16)
+        ok.bicgstab_multi(W2, b, mode=ok.SOLVE_MIXED16, net=net)
