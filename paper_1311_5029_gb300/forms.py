@@ -13,7 +13,8 @@ Each form prints one JSON line:
   [0.1, 0.3], then evaluated on 10 held-out fields against the unpreconditioned solver
   (iterations, wall time) and against plain FP64 BiCGStab.
 * ``large``: 28^3 x 96 (2.1 M sites): memory held and time to 1e-10 for the 12 sources with the
-  multi-RHS mixed-precision solve; plain FP64 timed on two sources and scaled to twelve.
+  multi-RHS mixed-precision solve, without and with a learned preconditioner (trained for this
+  mass and roughness on 16^3 x 32 fields); plain FP64 timed on two sources and scaled to twelve.
 
 Inputs are seeded synthetic fields (no gauge ensemble is available); times are wall-clock around
 the library call after one untimed warm-up solve, with the device synchronised on both sides.
@@ -101,21 +102,19 @@ def form_multi(quick=False):
     return out
 
 
-def form_net(quick=False, layers=4, epochs=6, lr=1e-2):
+def train_net(dims, am0, eps_list, per_field, layers=4, epochs=6, lr=1e-2, seed0=20000):
+    """Generate (source, solution) pairs with this library's multi-RHS solver on one synthetic field
+    per entry of eps_list and train a preconditioner network on them.  Returns (net, report)."""
     import torch
-    w = synth.WORKLOADS["16^3x32"]
-    dims = w["dims"]
-    c = synth.placeholder_coeffs(w["am0"])
-    nfields, per_field, nheld = (4, 24, 3) if quick else (20, 100, 10)
+    c = synth.placeholder_coeffs(am0)
     t_gen0 = time.perf_counter()
     pairs = []
-    for f in range(nfields):
-        eps = 0.1 + 0.2 * f / max(nfields - 1, 1)
-        W = ok.precompute_W(_links(dims, eps, 20000 + f), c, (1, 1, 1, 1), ok.W_F64 | ok.W_F16 | ok.W_LINKS)
+    for f, eps in enumerate(eps_list):
+        W = ok.precompute_W(_links(dims, eps, seed0 + f), c, (1, 1, 1, 1), ok.W_F64 | ok.W_F16 | ok.W_LINKS)
         bs, xs = [], []
         for j in range(0, per_field, 12):
             n = min(12, per_field - j)
-            b = _gaussian_sources(dims, n, 30000 + 1000 * f + j)
+            b = _gaussian_sources(dims, n, 10 * seed0 + 1000 * f + j)
             x, _ = ok.bicgstab_multi(W, b, tol=1e-8, mode=ok.SOLVE_MIXED16, delta=1e-2, check_every=8)
             bs.append(b.to(torch.complex64))
             xs.append(x.to(torch.complex64))
@@ -124,7 +123,7 @@ def form_net(quick=False, layers=4, epochs=6, lr=1e-2):
     t_gen = time.perf_counter() - t_gen0
     net = ok.Net(layers)
     batch = 4
-    steps = [(f, j) for f in range(nfields) for j in range(0, per_field - batch + 1, batch)]
+    steps = [(f, j) for f in range(len(pairs)) for j in range(0, per_field - batch + 1, batch)]
     rng = np.random.default_rng(0)
     per_epoch = []
     t_train0 = time.perf_counter()
@@ -144,6 +143,19 @@ def form_net(quick=False, layers=4, epochs=6, lr=1e-2):
     t_train = time.perf_counter() - t_train0
     del pairs
     torch.cuda.empty_cache()
+    return net, {"layers": layers, "train_fields": len(eps_list), "pairs": len(eps_list) * per_field, "epochs": epochs,
+                 "pair_generation_s": round(t_gen, 1), "training_s": round(t_train, 1), "loss_first": first,
+                 "loss_last": last, "loss_per_epoch": per_epoch}
+
+
+def form_net(quick=False, layers=4, epochs=6, lr=1e-2):
+    import torch
+    w = synth.WORKLOADS["16^3x32"]
+    dims = w["dims"]
+    c = synth.placeholder_coeffs(w["am0"])
+    nfields, per_field, nheld = (4, 24, 3) if quick else (20, 100, 10)
+    eps_list = [0.1 + 0.2 * f / max(nfields - 1, 1) for f in range(nfields)]
+    net, report = train_net(dims, w["am0"], eps_list, per_field, layers, epochs, lr)
     evals = []
     for h in range(nheld):
         eps = 0.1 + 0.2 * h / max(nheld - 1, 1)
@@ -160,31 +172,39 @@ def form_net(quick=False, layers=4, epochs=6, lr=1e-2):
                       "net_true_relres": ok.true_residual(W, b, xn)})
         del W, b
     mean = lambda key, i: float(np.mean([e[key][i] for e in evals]))  # noqa: E731
-    return {"form": "learned_preconditioner", "workload": "16^3x32", "layers": layers,
-            "train_fields": nfields, "pairs": nfields * per_field, "held_out": nheld, "epochs": epochs,
-            "pair_generation_s": round(t_gen, 1), "training_s": round(t_train, 1),
-            "loss_first": first, "loss_last": last, "loss_per_epoch": per_epoch,
-            "mean_iters": {"plain_mixed16": mean("plain_mixed16", 0), "net_mixed16": mean("net_mixed16", 0),
-                           "plain_f64": mean("plain_f64", 0)},
-            "mean_ms": {"plain_mixed16": mean("plain_mixed16", 1), "net_mixed16": mean("net_mixed16", 1),
-                        "plain_f64": mean("plain_f64", 1)},
-            "held_out_fields": evals}
+    out = {"form": "learned_preconditioner", "workload": "16^3x32", "held_out": nheld}
+    out.update(report)
+    out.update({"mean_iters": {"plain_mixed16": mean("plain_mixed16", 0), "net_mixed16": mean("net_mixed16", 0),
+                               "plain_f64": mean("plain_f64", 0)},
+                "mean_ms": {"plain_mixed16": mean("plain_mixed16", 1), "net_mixed16": mean("net_mixed16", 1),
+                            "plain_f64": mean("plain_f64", 1)},
+                "held_out_fields": evals})
+    return out
 
 
 def form_large(quick=False):
     import torch
     w = synth.WORKLOADS["28^3x96"]
     dims = w["dims"]
-    torch.cuda.reset_peak_memory_stats()
+    # the network for this mass and roughness, trained on 16^3 x 32 fields (it is local and
+    # translation invariant, so it carries over to the larger lattice)
+    small = synth.WORKLOADS["16^3x32"]["dims"]
+    nf = 3 if quick else 6
+    net, report = train_net(small, w["am0"], [w["eps"]] * nf, 24 if quick else 48, seed0=60000)
     free0, total = torch.cuda.mem_get_info()
     W = ok.precompute_W(_links(dims, w["eps"], w["seed"]), synth.placeholder_coeffs(w["am0"]), (1, 1, 1, 1),
-                        ok.W_F64 | ok.W_F16)
+                        ok.W_F64 | ok.W_F16 | ok.W_LINKS)
     b = spin_colour_sources(dims)
     nr, _ = ok.autotune(W, ok.F32_W16, nrhs=12)
     (x, infos), t_multi = _timed(lambda: ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED16, delta=1e-2,
                                                            check_every=8))
     worst = max(ok.true_residual(W, b[k].contiguous(), x[k].contiguous()) for k in range(12))
     free1, _ = torch.cuda.mem_get_info()
+    del x
+    (xn, infn), t_net = _timed(lambda: ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED16, delta=1e-2,
+                                                         check_every=8, net=net))
+    worst_net = max(ok.true_residual(W, b[k].contiguous(), xn[k].contiguous()) for k in range(12))
+    del xn
     nplain = 1 if quick else 2
     _sync()
     t0 = time.perf_counter()
@@ -197,8 +217,11 @@ def form_large(quick=False):
     return {"form": "large_lattice", "workload": "28^3x96, 12 spin-colour point sources",
             "sites": int(np.prod(dims)), "W_bytes": W.nbytes, "device_bytes_in_use_after_solve": int(total - free1),
             "device_bytes_total": int(total), "multi_ms": round(t_multi, 1), "multi_iters": [i["iters"] for i in infos],
-            "worst_true_relres": worst, "plain_f64_12_ms_scaled": round(t_plain, 1), "plain_f64_iters": iters,
-            "plain_sources_timed": nplain, "speedup_vs_plain_f64": round(t_plain / t_multi, 2), "rhs_per_thread": nr}
+            "worst_true_relres": worst, "multi_net_ms": round(t_net, 1), "multi_net_iters": [i["iters"] for i in infn],
+            "worst_true_relres_net": worst_net, "net_training": report,
+            "plain_f64_12_ms_scaled": round(t_plain, 1), "plain_f64_iters": iters, "plain_sources_timed": nplain,
+            "speedup_vs_plain_f64": round(t_plain / t_multi, 2), "speedup_net_vs_plain_f64": round(t_plain / t_net, 2),
+            "rhs_per_thread": nr}
 
 
 def main(argv=None):
