@@ -223,9 +223,9 @@ int ok_net_train_step(ok_net* net, const ok_W* W, int nb, const void* b, const v
                       double* loss, void* stream);
 int ok_bicgstab_net(const ok_W* W, ok_net* net, const void* src, void* x, const ok_solve_params* params,
                     ok_solve_info* info, void* stream);
-/* ok_bicgstab_multi with every system's FP32 iteration right-preconditioned by the network (the
- * network applied to each system in turn; arguments and results as ok_bicgstab_multi, the handle
- * needs OK_W_LINKS). */
+/* ok_bicgstab_multi with every system's FP32 iteration right-preconditioned by the network (one
+ * launch per network layer for all systems; arguments and results as ok_bicgstab_multi, the
+ * handle needs OK_W_LINKS; the solve allocates four more FP32 fields per system). */
 int ok_bicgstab_multi_net(const ok_W* W, ok_net* net, int nrhs, const void* src, void* x,
                           const ok_solve_params* params, ok_solve_info* info, void* stream);
 

@@ -95,6 +95,8 @@ void net_free(ok_net* N);
 int net_weights(ok_net* N, double* get, const double* set);
 int net_layers(const ok_net* N);
 int net_apply(ok_net* N, const ok_W* W, const cx<float>* in, cx<float>* out, cudaStream_t st);
+int net_apply_multi(ok_net* N, const ok_W* W, const cx<float>* in, cx<float>* out, int nrhs, cx<float>* tmp0, cx<float>* tmp1,
+                    cudaStream_t st);
 int net_loss_grad(ok_net* N, const ok_W* W, const cx<float>* b, const cx<float>* x, double* loss, double* grad, cudaStream_t st);
 int net_train_step(ok_net* N, const ok_W* W, int nb, const cx<float>* b, const cx<float>* x, double lr, double* loss,
                    cudaStream_t st);

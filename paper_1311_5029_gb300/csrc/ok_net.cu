@@ -112,11 +112,14 @@ __device__ __forceinline__ void transported(const cx<float>* __restrict__ L, con
   }
 }
 
-// out = sum_d A_d T_d in   (ADJ: sum_d A_d^dag T_{-d} in, the adjoint layer)
+// out = sum_d A_d T_d in   (ADJ: sum_d A_d^dag T_{-d} in, the adjoint layer).  Grid row
+// blockIdx.y works on the field at in + blockIdx.y * rs (several right-hand sides per launch).
 template <bool ADJ>
 __global__ void __launch_bounds__(NET_THREADS) net_layer_kernel(const cx<float>* __restrict__ L, const float2* __restrict__ A,
                                                                 const cx<float>* __restrict__ in, cx<float>* __restrict__ out,
-                                                                Geom g) {
+                                                                Geom g, long long rs) {
+  in += blockIdx.y * rs;
+  out += blockIdx.y * rs;
   __shared__ float2 sA[NOFF * 16];
   for (int i = threadIdx.x; i < NOFF * 16; i += NET_THREADS) {
     if (!ADJ) {
@@ -277,16 +280,17 @@ int ensure_workspace(ok_net* N, int V) {
   return OK_SUCCESS;
 }
 
-int layer(const ok_net* N, const ok_W* W, int l, bool adj, const cx<float>* in, cx<float>* out, cudaStream_t st) {
+int layer(const ok_net* N, const ok_W* W, int l, bool adj, const cx<float>* in, cx<float>* out, cudaStream_t st,
+          int nrhs = 1) {
   const Geom& g = W->g;
+  const dim3 grid(grid_for(g.V, NET_THREADS), nrhs);
+  const long long rs = 12LL * g.V;
   {
     TraceScope ts(adj ? "net_layer_adj" : "net_layer", st);
     if (adj)
-      net_layer_kernel<true><<<grid_for(g.V, NET_THREADS), NET_THREADS, 0, st>>>((const cx<float>*)W->L32, N->A + (size_t)l * 144, in,
-                                                                                out, g);
+      net_layer_kernel<true><<<grid, NET_THREADS, 0, st>>>((const cx<float>*)W->L32, N->A + (size_t)l * 144, in, out, g, rs);
     else
-      net_layer_kernel<false><<<grid_for(g.V, NET_THREADS), NET_THREADS, 0, st>>>((const cx<float>*)W->L32, N->A + (size_t)l * 144,
-                                                                                 in, out, g);
+      net_layer_kernel<false><<<grid, NET_THREADS, 0, st>>>((const cx<float>*)W->L32, N->A + (size_t)l * 144, in, out, g, rs);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
@@ -359,6 +363,22 @@ int net_apply(ok_net* N, const ok_W* W, const cx<float>* in, cx<float>* out, cud
   for (int l = 0; l < N->layers; ++l) {
     cx<float>* o = l == N->layers - 1 ? out : N->g[l % 2];  // ping-pong through the workspace
     NET_TRY(layer(N, W, l, false, cur, o, st));
+    cur = o;
+  }
+  return OK_SUCCESS;
+}
+
+// out_k = P in_k for nrhs fields [nrhs][V][12] in one launch per layer, through the caller's two
+// scratch fields of the same size.
+int net_apply_multi(ok_net* N, const ok_W* W, const cx<float>* in, cx<float>* out, int nrhs, cx<float>* tmp0, cx<float>* tmp1,
+                    cudaStream_t st) {
+  NET_TRY(check(N, W));
+  if (nrhs < 1 || nrhs > 65535 || !tmp0 || !tmp1) return OK_EINVAL;
+  cx<float>* tmp[2] = {tmp0, tmp1};
+  const cx<float>* cur = in;
+  for (int l = 0; l < N->layers; ++l) {
+    cx<float>* o = l == N->layers - 1 ? out : tmp[l % 2];
+    NET_TRY(layer(N, W, l, false, cur, o, st, nrhs));
     cur = o;
   }
   return OK_SUCCESS;

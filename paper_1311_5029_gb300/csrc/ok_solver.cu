@@ -389,7 +389,9 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
   b.t = ws.get<cx<float>>(N, &err);
   cx<float>* zp = net ? ws.get<cx<float>>(N, &err) : nullptr;  // P p and P s of every system
   cx<float>* zs = net ? ws.get<cx<float>>(N, &err) : nullptr;
-  if (net && (!zp || !zs)) { set_cuda_error(err); return OK_ENOMEM; }
+  cx<float>* nt0 = net ? ws.get<cx<float>>(N, &err) : nullptr;  // the network's layer scratch
+  cx<float>* nt1 = net ? ws.get<cx<float>>(N, &err) : nullptr;
+  if (net && (!zp || !zs || !nt0 || !nt1)) { set_cuda_error(err); return OK_ENOMEM; }
   SolverState* h = nullptr;
   if (cudaMallocHost((void**)&h, sizeof(SolverState) * nrhs) != cudaSuccess) h = nullptr;
   struct HostFree { SolverState* p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{h};
@@ -442,20 +444,20 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
   }
 
   const MultiShape shape = multi_shape(W, w16, nrhs);
-  // One iteration for every system; with a right preconditioner P (applied to each system in
-  // turn) the operator is M P, as in iterate() above.
+  // One iteration for every system; with a right preconditioner P (one launch per network layer
+  // for all systems) the operator is M P, as in iterate() above.
   auto iterate_all = [&]() -> int {
     const cx<float>* pin = b.p;
     const cx<float>* sin = b.s;
     if (net) {
-      for (int k = 0; k < nrhs; ++k) OK_TRY(net_apply(net, W, vec(b.p, k), vec(zp, k), st));
+      OK_TRY(net_apply_multi(net, W, b.p, zp, nrhs, nt0, nt1, st));
       pin = zp;
     }
     MultiEpi e1{b.rhat, dst, part, pstride, FIN_ALPHA, 0};
     OK_TRY(launch_apply_multi(W, w16, pin, b.v, nrhs, EPI_DOT, e1, shape, st));
     OK_TRY(launch_update_s_multi(b.r, b.v, b.s, n, nrhs, dst, st));
     if (net) {
-      for (int k = 0; k < nrhs; ++k) OK_TRY(net_apply(net, W, vec(b.s, k), vec(zs, k), st));
+      OK_TRY(net_apply_multi(net, W, b.s, zs, nrhs, nt0, nt1, st));
       sin = zs;
     }
     MultiEpi e2{net ? b.s : nullptr, dst, part, pstride, FIN_OMEGA, 1};
