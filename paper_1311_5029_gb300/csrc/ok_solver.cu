@@ -31,14 +31,18 @@ namespace okgb {
 namespace {
 
 struct Workspace {
+  static constexpr int CAP = 32;
   cudaStream_t st = nullptr;
-  void* mem[12] = {};
+  void* mem[CAP] = {};
   int n = 0;
   ~Workspace() {
     for (int k = 0; k < n; ++k)
       if (mem[k]) cudaFreeAsync(mem[k], st);
   }
+  // Stream-ordered allocation released with the workspace; null (with *err set) on failure or
+  // when the workspace's CAP buffers are taken.
   template <typename T> T* get(size_t count, cudaError_t* err) {
+    if (n >= CAP) { *err = cudaErrorMemoryAllocation; return nullptr; }
     void* p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), st);
     if (e != cudaSuccess) { *err = e; return nullptr; }
