@@ -112,14 +112,16 @@ __device__ __forceinline__ void transported(const cx<float>* __restrict__ L, con
   }
 }
 
-// out = sum_d A_d T_d in   (ADJ: sum_d A_d^dag T_{-d} in, the adjoint layer).  Grid row
-// blockIdx.y works on the field at in + blockIdx.y * rs (several right-hand sides per launch).
+// out = sum_d A_d T_d in   (ADJ: sum_d A_d^dag T_{-d} in, the adjoint layer).  With nrhs fields
+// [nrhs][V][12] per launch, block b works on field b % nrhs and site block b / nrhs, so the blocks
+// that read the same links run back to back and share them through L2.
 template <bool ADJ>
 __global__ void __launch_bounds__(NET_THREADS) net_layer_kernel(const cx<float>* __restrict__ L, const float2* __restrict__ A,
                                                                 const cx<float>* __restrict__ in, cx<float>* __restrict__ out,
-                                                                Geom g, long long rs) {
-  in += blockIdx.y * rs;
-  out += blockIdx.y * rs;
+                                                                Geom g, int nrhs) {
+  const int rhs = blockIdx.x % nrhs, sb = blockIdx.x / nrhs;
+  in += (size_t)rhs * 12 * g.V;
+  out += (size_t)rhs * 12 * g.V;
   __shared__ float2 sA[NOFF * 16];
   for (int i = threadIdx.x; i < NOFF * 16; i += NET_THREADS) {
     if (!ADJ) {
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(NET_THREADS) net_layer_kernel(const cx<float>*
     }
   }
   __syncthreads();
-  const int x = blockIdx.x * NET_THREADS + threadIdx.x;
+  const int x = sb * NET_THREADS + threadIdx.x;
   if (x >= g.V) return;
   int c[4];
   site_coords(x, g, c);
@@ -283,14 +285,14 @@ int ensure_workspace(ok_net* N, int V) {
 int layer(const ok_net* N, const ok_W* W, int l, bool adj, const cx<float>* in, cx<float>* out, cudaStream_t st,
           int nrhs = 1) {
   const Geom& g = W->g;
-  const dim3 grid(grid_for(g.V, NET_THREADS), nrhs);
-  const long long rs = 12LL * g.V;
+  const long long nb = (long long)grid_for(g.V, NET_THREADS) * nrhs;
+  if (nb > 0x7fffffffLL) return OK_EINVAL;
   {
     TraceScope ts(adj ? "net_layer_adj" : "net_layer", st);
     if (adj)
-      net_layer_kernel<true><<<grid, NET_THREADS, 0, st>>>((const cx<float>*)W->L32, N->A + (size_t)l * 144, in, out, g, rs);
+      net_layer_kernel<true><<<(unsigned)nb, NET_THREADS, 0, st>>>((const cx<float>*)W->L32, N->A + (size_t)l * 144, in, out, g, nrhs);
     else
-      net_layer_kernel<false><<<grid, NET_THREADS, 0, st>>>((const cx<float>*)W->L32, N->A + (size_t)l * 144, in, out, g, rs);
+      net_layer_kernel<false><<<(unsigned)nb, NET_THREADS, 0, st>>>((const cx<float>*)W->L32, N->A + (size_t)l * 144, in, out, g, nrhs);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
