@@ -122,46 +122,58 @@ __global__ void __launch_bounds__(NET_THREADS) net_layer_kernel(const cx<float>*
   const int rhs = blockIdx.x % nrhs, sb = blockIdx.x / nrhs;
   in += (size_t)rhs * 12 * g.V;
   out += (size_t)rhs * 12 * g.V;
-  __shared__ float2 sA[NOFF * 16];
+  // Each weight a is kept as (a.re, a.re, -a.im, a.im), so that a w adds to (re, im) as two
+  // packed FP32 multiply-adds: (a.re, a.re) * (w.re, w.im) + (-a.im, a.im) * (w.im, w.re).
+  __shared__ float4 sA[NOFF * 16];
   for (int i = threadIdx.x; i < NOFF * 16; i += NET_THREADS) {
+    float2 a;
     if (!ADJ) {
-      sA[i] = A[i];
+      a = A[i];
     } else {
       const int d = i / 16, s = (i % 16) / 4, t = i % 4;
-      const float2 a = A[d * 16 + t * 4 + s];
-      sA[i] = make_float2(a.x, -a.y);
+      const float2 b = A[d * 16 + t * 4 + s];
+      a = make_float2(b.x, -b.y);
     }
+    sA[i] = make_float4(a.x, a.x, -a.y, a.y);
   }
   __syncthreads();
   const int x = sb * NET_THREADS + threadIdx.x;
   if (x >= g.V) return;
   int c[4];
   site_coords(x, g, c);
-  cx<float> acc[4][3];
+  float2 acc[4][3];
 #pragma unroll
   for (int s = 0; s < 4; ++s)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) acc[s][a] = mk<float>(0.f, 0.f);
+    for (int a = 0; a < 3; ++a) acc[s][a] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int d = 0; d < NOFF; ++d) {
     cx<float> w[4][3];
     transported<ADJ>(L, in, x, c, g, d, w);
+    float2 wv[4][3], ws[4][3];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        wv[t][k] = make_float2(w[t][k].re, w[t][k].im);
+        ws[t][k] = make_float2(w[t][k].im, w[t][k].re);
+      }
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const float2 a2 = sA[d * 16 + s * 4 + t];
-        const cx<float> a = mk<float>(a2.x, a2.y);
+        const float4 a4 = sA[d * 16 + s * 4 + t];
+        const float2 ar = make_float2(a4.x, a4.y), ai = make_float2(a4.z, a4.w);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) acc[s][k] = fma_c(a, w[t][k], acc[s][k]);
+        for (int k = 0; k < 3; ++k) acc[s][k] = __ffma2_rn(ai, ws[t][k], __ffma2_rn(ar, wv[t][k], acc[s][k]));
       }
   }
   float4* q = reinterpret_cast<float4*>(out) + (size_t)x * 6;
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    const cx<float>& u = acc[(2 * k) / 3][(2 * k) % 3];
-    const cx<float>& v = acc[(2 * k + 1) / 3][(2 * k + 1) % 3];
-    q[k] = make_float4(u.re, u.im, v.re, v.im);
+    const float2 u = acc[(2 * k) / 3][(2 * k) % 3];
+    const float2 v = acc[(2 * k + 1) / 3][(2 * k + 1) % 3];
+    q[k] = make_float4(u.x, u.y, v.x, v.y);
   }
 }
 
