@@ -30,6 +30,10 @@ import numpy as np
 import synth
 import paper_1311_5029_gb300 as ok
 
+# Reliable-update threshold of the timed mixed-precision solves (the FP32 residual must drop by
+# this factor before an FP64 residual is recomputed); set by --delta.
+DELTA = 1e-4
+
 
 def _sync():
     import torch
@@ -79,8 +83,8 @@ def form_multi(quick=False):
         W = ok.precompute_W(U, synth.placeholder_coeffs(am0), (1, 1, 1, 1), ok.W_F64 | ok.W_F16)
         b = spin_colour_sources(dims)
         nr, us = ok.autotune(W, ok.F32_W16, nrhs=12)
-        ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED16, delta=1e-2, check_every=8)
-        (x, infos), t_multi = _timed(lambda: ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED16, delta=1e-2,
+        ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED16, delta=DELTA, check_every=8)
+        (x, infos), t_multi = _timed(lambda: ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED16, delta=DELTA,
                                                                check_every=8))
         worst = max(ok.true_residual(W, b[k].contiguous(), x[k].contiguous()) for k in range(12))
         nplain = 2 if quick else 12
@@ -196,12 +200,12 @@ def form_large(quick=False):
                         ok.W_F64 | ok.W_F16 | ok.W_LINKS)
     b = spin_colour_sources(dims)
     nr, _ = ok.autotune(W, ok.F32_W16, nrhs=12)
-    (x, infos), t_multi = _timed(lambda: ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED16, delta=1e-2,
+    (x, infos), t_multi = _timed(lambda: ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED16, delta=DELTA,
                                                            check_every=8))
     worst = max(ok.true_residual(W, b[k].contiguous(), x[k].contiguous()) for k in range(12))
     free1, _ = torch.cuda.mem_get_info()
     del x
-    (xn, infn), t_net = _timed(lambda: ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED16, delta=1e-2,
+    (xn, infn), t_net = _timed(lambda: ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED16, delta=DELTA,
                                                          check_every=8, net=net))
     worst_net = max(ok.true_residual(W, b[k].contiguous(), xn[k].contiguous()) for k in range(12))
     del xn
@@ -228,7 +232,9 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--form", default="all", choices=["multi", "net", "large", "all"])
     ap.add_argument("--quick", action="store_true", help="smaller samples (a smoke run)")
+    ap.add_argument("--delta", type=float, default=DELTA, help="reliable-update threshold of the timed solves")
     a = ap.parse_args(argv)
+    globals()["DELTA"] = a.delta
     forms = ["multi", "net", "large"] if a.form == "all" else [a.form]
     for f in forms:
         res = {"multi": form_multi, "net": form_net, "large": form_large}[f](quick=a.quick)
