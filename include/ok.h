@@ -195,8 +195,8 @@ int ok_autotune(ok_W* W, ok_prec prec, int nrhs, int* choice, double* best_us, v
  *
  * Weights are host arrays of layers * 288 doubles: complex128 [layers][9 offsets][4][4] as
  * (re, im) pairs, offsets in the order above.  The network keeps FP32 weights, Adam moments and a
- * workspace of (layers + 2) V 96 bytes, allocated at first use; one network must not be used from
- * two streams at once.
+ * workspace allocated at first use: 2 V 96 bytes for applications, plus layers V 96 bytes once it
+ * trains.  One network must not be used from two streams at once.
  *
  * ok_net_create: layers 1..16, weights NULL for the identity (A_0 = 1).  ok_net_free releases it.
  * ok_net_apply: out = P psi; psi, out: device [V][4][3] complex64, not overlapping.

@@ -33,7 +33,7 @@ struct ok_net {
   long long adam_t = 0;
   int V = 0;                // volume the workspace is sized for
   int device = 0;
-  okgb::cx<float>* acts = nullptr;  // [layers][V * 12]
+  okgb::cx<float>* acts = nullptr;  // [layers][V * 12], training only
   okgb::cx<float>* g[2] = {nullptr, nullptr};
   double* part = nullptr;     // [blocks][9][32]
   int part_blocks = 0;
@@ -274,23 +274,27 @@ int net_blocks(int V) {
   return need < cap ? need : cap;
 }
 
-int ensure_workspace(ok_net* N, int V) {
-  if (N->V == V && N->acts) return OK_SUCCESS;
-  if (N->acts) cudaFree(N->acts);
-  if (N->g[0]) cudaFree(N->g[0]);
-  if (N->g[1]) cudaFree(N->g[1]);
-  if (N->part) cudaFree(N->part);
-  N->acts = nullptr; N->g[0] = N->g[1] = nullptr; N->part = nullptr; N->V = 0;
+// Scratch for a lattice of V sites: two fields (the layer ping-pong and the backward gradients),
+// the reduction partials, and, for training, the activations of every layer.
+int ensure_workspace(ok_net* N, int V, bool training) {
+  if (N->V == V && N->g[0] && (!training || N->acts)) return OK_SUCCESS;
   const size_t n = (size_t)V * 12;
-  OK_CUDA_TRY(cudaMalloc(&N->acts, (size_t)N->layers * n * sizeof(cx<float>)));
-  OK_CUDA_TRY(cudaMalloc(&N->g[0], n * sizeof(cx<float>)));
-  OK_CUDA_TRY(cudaMalloc(&N->g[1], n * sizeof(cx<float>)));
-  N->part_blocks = net_blocks(V);
-  const int lb = grid_for((long long)n, 256) < 1024 ? grid_for((long long)n, 256) : 1024;
-  size_t pn = (size_t)N->part_blocks * NPAR;
-  if ((size_t)lb * 2 > pn) pn = (size_t)lb * 2;
-  OK_CUDA_TRY(cudaMalloc(&N->part, pn * sizeof(double)));
-  N->V = V;
+  if (N->V != V) {
+    if (N->acts) cudaFree(N->acts);
+    if (N->g[0]) cudaFree(N->g[0]);
+    if (N->g[1]) cudaFree(N->g[1]);
+    if (N->part) cudaFree(N->part);
+    N->acts = nullptr; N->g[0] = N->g[1] = nullptr; N->part = nullptr; N->V = 0;
+    OK_CUDA_TRY(cudaMalloc(&N->g[0], n * sizeof(cx<float>)));
+    OK_CUDA_TRY(cudaMalloc(&N->g[1], n * sizeof(cx<float>)));
+    N->part_blocks = net_blocks(V);
+    const int lb = grid_for((long long)n, 256) < 1024 ? grid_for((long long)n, 256) : 1024;
+    size_t pn = (size_t)N->part_blocks * NPAR;
+    if ((size_t)lb * 2 > pn) pn = (size_t)lb * 2;
+    OK_CUDA_TRY(cudaMalloc(&N->part, pn * sizeof(double)));
+    N->V = V;
+  }
+  if (training && !N->acts) OK_CUDA_TRY(cudaMalloc(&N->acts, (size_t)N->layers * n * sizeof(cx<float>)));
   return OK_SUCCESS;
 }
 
@@ -370,9 +374,7 @@ int check(const ok_net* N, const ok_W* W) {
 
 int net_apply(ok_net* N, const ok_W* W, const cx<float>* in, cx<float>* out, cudaStream_t st) {
   NET_TRY(check(N, W));
-  NET_TRY(ensure_workspace(N, W->g.V));
-  const long long n = 12LL * W->g.V;
-  (void)n;
+  NET_TRY(ensure_workspace(N, W->g.V, false));
   const cx<float>* cur = in;
   for (int l = 0; l < N->layers; ++l) {
     cx<float>* o = l == N->layers - 1 ? out : N->g[l % 2];  // ping-pong through the workspace
@@ -400,7 +402,7 @@ int net_apply_multi(ok_net* N, const ok_W* W, const cx<float>* in, cx<float>* ou
 
 int net_loss_grad(ok_net* N, const ok_W* W, const cx<float>* b, const cx<float>* x, double* loss, double* grad, cudaStream_t st) {
   NET_TRY(check(N, W));
-  NET_TRY(ensure_workspace(N, W->g.V));
+  NET_TRY(ensure_workspace(N, W->g.V, true));
   OK_CUDA_TRY(cudaMemsetAsync(N->gacc, 0, sizeof(double) * NPAR * N->layers, st));
   OK_CUDA_TRY(cudaMemsetAsync(N->scal, 0, sizeof(double) * 4, st));
   NET_TRY(pair_backprop(N, W, b, x, st));
@@ -416,7 +418,7 @@ int net_train_step(ok_net* N, const ok_W* W, int nb, const cx<float>* b, const c
                    cudaStream_t st) {
   NET_TRY(check(N, W));
   if (nb < 1 || !b || !x || !(lr > 0.0)) return OK_EINVAL;
-  NET_TRY(ensure_workspace(N, W->g.V));
+  NET_TRY(ensure_workspace(N, W->g.V, true));
   const long long n = 12LL * W->g.V;
   OK_CUDA_TRY(cudaMemsetAsync(N->gacc, 0, sizeof(double) * NPAR * N->layers, st));
   OK_CUDA_TRY(cudaMemsetAsync(N->scal, 0, sizeof(double) * 4, st));
