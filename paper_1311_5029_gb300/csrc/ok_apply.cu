@@ -546,10 +546,6 @@ static_assert(SPLIT_SITES == LANES, "a tile is one site block of the W layout");
 #ifndef OK_STAGES
 #define OK_STAGES 2
 #endif
-// FP32 hops with packed FMAs and split accumulators (1) or with scalar FMAs (0).
-#ifndef OK_FFMA2
-#define OK_FFMA2 1
-#endif
 constexpr int NCHUNK = 7;     // W0 | W+t | W+x | W+y | W+z | W++ii | W++ij, W+-ij
 constexpr int CHUNK_MAX = 8;  // matrices in the largest chunk
 __device__ __forceinline__ int chunk_first(int c) {
@@ -745,71 +741,44 @@ __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB
     c[1] = r % g.L[1]; r /= g.L[1];
     c[2] = r % g.L[2]; c[3] = r / g.L[2];
   }
-  // FP32 fields: the packed-FMA hop functions with a split accumulator (ok_pair.cuh).
-  constexpr bool F2 = OK_FFMA2 && std::is_same<R, float>::value;
-  Acc2 a2;
-  if constexpr (F2) acc2_zero(a2);
-  // Forward hop calls, packed or plain.
-  auto fw_time = [&](const auto& w) {
-    if constexpr (F2) f2_time<true>(w, psi, c, g, s, pr, a2); else pair_time<R, true, false>(w, psi, c, g, s, pr, acc);
-  };
-  auto fw_spatial = [&](const auto& w, auto I) {
-    if constexpr (F2) f2_spatial<decltype(I)::value, true>(w, psi, c, g, s, pr, a2);
-    else pair_spatial<R, decltype(I)::value, true, false>(w, psi, c, g, s, pr, acc);
-  };
-  auto fw_two = [&](const auto& w) {
-    if constexpr (F2) {
-      f2_two<0, true>(w, psi, c, g, s, pr, a_ii, b_ii, a2);
-      f2_two<1, true>(w, psi, c, g, s, pr, a_ii, b_ii, a2);
-      f2_two<2, true>(w, psi, c, g, s, pr, a_ii, b_ii, a2);
-    } else {
-      pair_two<R, 0, true, false>(w, psi, c, g, s, pr, a_ii, b_ii, acc);
-      pair_two<R, 1, true, false>(w, psi, c, g, s, pr, a_ii, b_ii, acc);
-      pair_two<R, 2, true, false>(w, psi, c, g, s, pr, a_ii, b_ii, acc);
-    }
-  };
-  auto fw_diag = [&](const auto& w) {
-    if constexpr (F2) {
-      f2_diag<0, 1, 0, true>(w, psi, c, g, s, pr, a2);
-      f2_diag<0, 2, 1, true>(w, psi, c, g, s, pr, a2);
-      f2_diag<1, 2, 2, true>(w, psi, c, g, s, pr, a2);
-    } else {
-      pair_diag<R, 0, 1, 0, true, false>(w, psi, c, g, s, pr, acc);
-      pair_diag<R, 0, 2, 1, true, false>(w, psi, c, g, s, pr, acc);
-      pair_diag<R, 1, 2, 2, true, false>(w, psi, c, g, s, pr, acc);
-    }
-  };
-  // The on-site term starts the accumulator (in split form: Y = acc, Z = 0).
-  auto fw_onsite = [&](const auto& w) {
-    pair_onsite<R>(w, psi, s, pr, c0q, acc);
-    if constexpr (F2) {
-#pragma unroll
-      for (int qq = 0; qq < 2; ++qq)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) a2.Y[qq][k] = make_float2(acc.v[qq][k].re, acc.v[qq][k].im);
-    }
-  };
   if (half == 0) {
     if constexpr (STAGED) {
       // Every forward thread takes part in the waits and barriers, active or not.
-      { auto w = chunk(M_Y0P); if (active) fw_onsite(w); release(); }
-      { auto w = chunk(M_UT); if (active) fw_time(w); release(); }
-      { auto w = chunk(M_WP + 0); if (active) fw_spatial(w, std::integral_constant<int, 0>()); release(); }
-      { auto w = chunk(M_WP + 8); if (active) fw_spatial(w, std::integral_constant<int, 1>()); release(); }
-      { auto w = chunk(M_WP + 16); if (active) fw_spatial(w, std::integral_constant<int, 2>()); release(); }
-      { auto w = chunk(M_VII); if (active) fw_two(w); release(); }
-      { auto w = chunk(M_VIJ); if (active) fw_diag(w); release(); }
+      { auto w = chunk(M_Y0P); if (active) pair_onsite<R>(w, psi, s, pr, c0q, acc); release(); }
+      { auto w = chunk(M_UT); if (active) pair_time<R, true, false>(w, psi, c, g, s, pr, acc); release(); }
+      { auto w = chunk(M_WP + 0); if (active) pair_spatial<R, 0, true, false>(w, psi, c, g, s, pr, acc); release(); }
+      { auto w = chunk(M_WP + 8); if (active) pair_spatial<R, 1, true, false>(w, psi, c, g, s, pr, acc); release(); }
+      { auto w = chunk(M_WP + 16); if (active) pair_spatial<R, 2, true, false>(w, psi, c, g, s, pr, acc); release(); }
+      {
+        auto w = chunk(M_VII);
+        if (active) {
+          pair_two<R, 0, true, false>(w, psi, c, g, s, pr, a_ii, b_ii, acc);
+          pair_two<R, 1, true, false>(w, psi, c, g, s, pr, a_ii, b_ii, acc);
+          pair_two<R, 2, true, false>(w, psi, c, g, s, pr, a_ii, b_ii, acc);
+        }
+        release();
+      }
+      {
+        auto w = chunk(M_VIJ);
+        if (active) {
+          pair_diag<R, 0, 1, 0, true, false>(w, psi, c, g, s, pr, acc);
+          pair_diag<R, 0, 2, 1, true, false>(w, psi, c, g, s, pr, acc);
+          pair_diag<R, 1, 2, 2, true, false>(w, psi, c, g, s, pr, acc);
+        }
+        release();
+      }
     } else if (active) {
-      fw_onsite(Wg);
-      fw_spatial(Wg, std::integral_constant<int, 0>());
-      fw_spatial(Wg, std::integral_constant<int, 1>());
-      fw_spatial(Wg, std::integral_constant<int, 2>());
-      fw_time(Wg);
-      fw_two(Wg);
-      fw_diag(Wg);
-    }
-    if constexpr (F2) {
-      if (active) acc2_combine<false>(a2, acc);
+      pair_onsite<R>(Wg, psi, s, pr, c0q, acc);
+      pair_spatial<R, 0, true, false>(Wg, psi, c, g, s, pr, acc);
+      pair_spatial<R, 1, true, false>(Wg, psi, c, g, s, pr, acc);
+      pair_spatial<R, 2, true, false>(Wg, psi, c, g, s, pr, acc);
+      pair_time<R, true, false>(Wg, psi, c, g, s, pr, acc);
+      pair_two<R, 0, true, false>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_two<R, 1, true, false>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_two<R, 2, true, false>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_diag<R, 0, 1, 0, true, false>(Wg, psi, c, g, s, pr, acc);
+      pair_diag<R, 0, 2, 1, true, false>(Wg, psi, c, g, s, pr, acc);
+      pair_diag<R, 1, 2, 2, true, false>(Wg, psi, c, g, s, pr, acc);
     }
   } else if (active) {
       // The epilogue's own half-spinor (rhat, b, or the y of <out, y>) is copied into shared memory
@@ -824,30 +793,16 @@ __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB
                        : "memory");
         asm volatile("cp.async.commit_group;" ::: "memory");
       }
-      if constexpr (F2) {
-        f2_spatial<0, false>(Wg, psi, c, g, s, pr, a2);
-        f2_spatial<1, false>(Wg, psi, c, g, s, pr, a2);
-        f2_spatial<2, false>(Wg, psi, c, g, s, pr, a2);
-        f2_time<false>(Wg, psi, c, g, s, pr, a2);
-        f2_two<0, false>(Wg, psi, c, g, s, pr, a_ii, b_ii, a2);
-        f2_two<1, false>(Wg, psi, c, g, s, pr, a_ii, b_ii, a2);
-        f2_two<2, false>(Wg, psi, c, g, s, pr, a_ii, b_ii, a2);
-        f2_diag<0, 1, 0, false>(Wg, psi, c, g, s, pr, a2);
-        f2_diag<0, 2, 1, false>(Wg, psi, c, g, s, pr, a2);
-        f2_diag<1, 2, 2, false>(Wg, psi, c, g, s, pr, a2);
-        acc2_combine<true>(a2, acc);
-      } else {
-        pair_spatial<R, 0, false, true>(Wg, psi, c, g, s, pr, acc);
-        pair_spatial<R, 1, false, true>(Wg, psi, c, g, s, pr, acc);
-        pair_spatial<R, 2, false, true>(Wg, psi, c, g, s, pr, acc);
-        pair_time<R, false, true>(Wg, psi, c, g, s, pr, acc);
-        pair_two<R, 0, false, true>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
-        pair_two<R, 1, false, true>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
-        pair_two<R, 2, false, true>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
-        pair_diag<R, 0, 1, 0, false, true>(Wg, psi, c, g, s, pr, acc);
-        pair_diag<R, 0, 2, 1, false, true>(Wg, psi, c, g, s, pr, acc);
-        pair_diag<R, 1, 2, 2, false, true>(Wg, psi, c, g, s, pr, acc);
-      }
+      pair_spatial<R, 0, false, true>(Wg, psi, c, g, s, pr, acc);
+      pair_spatial<R, 1, false, true>(Wg, psi, c, g, s, pr, acc);
+      pair_spatial<R, 2, false, true>(Wg, psi, c, g, s, pr, acc);
+      pair_time<R, false, true>(Wg, psi, c, g, s, pr, acc);
+      pair_two<R, 0, false, true>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_two<R, 1, false, true>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_two<R, 2, false, true>(Wg, psi, c, g, s, pr, a_ii, b_ii, acc);
+      pair_diag<R, 0, 1, 0, false, true>(Wg, psi, c, g, s, pr, acc);
+      pair_diag<R, 0, 2, 1, false, true>(Wg, psi, c, g, s, pr, acc);
+      pair_diag<R, 1, 2, 2, false, true>(Wg, psi, c, g, s, pr, acc);
 #pragma unroll
       for (int qq = 0; qq < 2; ++qq)
 #pragma unroll

@@ -451,193 +451,4 @@ __device__ __forceinline__ void pair_onsite(const WS& W, const cx<R>* __restrict
     for (int k = 0; k < 3; ++k) acc.v[q][k] = (Rm.v[q][k] + Rp.v[q][k]) + ti(Rm.v[q][k] - Rp.v[q][k]);
 }
 
-
-// ============================================================================ packed FP32 hops
-// The same hops as above for FP32 fields, written so that every contribution is a colour
-// matrix-vector product accumulated with packed FP32 FMAs (__ffma2_rn, two lanes per
-// instruction).  A thread keeps its half-spinor accumulator in split form: for each component
-//   Y += A_e (v.re, v.re)  and  Z += A_e (v.im, v.im),   A_e = (re, im) of a matrix element,
-// so that A v = (Y.x - Z.y, Y.y + Z.x) and A^dag v = (Y.x + Z.y, Z.x - Y.y).  The forward
-// warps only ever add A v terms and the backward warps only A^dag v terms, so each keeps one
-// split accumulator and combines it once per tile.  The spin structure of the temporal, two-hop
-// and diagonal terms (the sign of the thread's projection, a +- b sigma_i, sigma_i +- sigma_j)
-// acts on spin only and commutes with the colour matrix, so it is applied to the gathered
-// half-spinor before the product.
-struct Acc2 { float2 Y[2][3], Z[2][3]; };
-struct Bc6 { float2 r[2][3], i[2][3]; };  // (re, re) and (im, im) of each component
-
-__device__ __forceinline__ void acc2_zero(Acc2& a) {
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) a.Y[q][k] = a.Z[q][k] = make_float2(0.f, 0.f);
-}
-
-// s h broadcast component-wise.
-__device__ __forceinline__ Bc6 bcast(const H6<float>& h, float s = 1.f) {
-  Bc6 b;
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float re = s * h.v[q][k].re, im = s * h.v[q][k].im;
-      b.r[q][k] = make_float2(re, re);
-      b.i[q][k] = make_float2(im, im);
-    }
-  return b;
-}
-
-// Row qo of the accumulator += (or -= when NEG) A (DAG: A^dag) times spin component qi of b.
-template <bool DAG, bool NEG>
-__device__ __forceinline__ void mvs(Acc2& a, int qo, const M3<float>& A, const Bc6& b, int qi) {
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const cx<float> e = DAG ? A.e[3 * c + k] : A.e[3 * k + c];
-      const float2 m = NEG ? make_float2(-e.re, -e.im) : make_float2(e.re, e.im);
-      a.Y[qo][k] = __ffma2_rn(m, b.r[qi][c], a.Y[qo][k]);
-      a.Z[qo][k] = __ffma2_rn(m, b.i[qi][c], a.Z[qo][k]);
-    }
-}
-
-// Split accumulator -> complex half-spinor (A v form for the forward warps, A^dag v otherwise).
-template <bool DAG>
-__device__ __forceinline__ void acc2_combine(const Acc2& a, H6<float>& out) {
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float2 Y = a.Y[q][k], Z = a.Z[q][k];
-      out.v[q][k] = DAG ? mk<float>(Y.x + Z.y, Z.x - Y.y) : mk<float>(Y.x - Z.y, Y.y + Z.x);
-    }
-}
-
-// sigma_k acting on the two spin components of h (the Pauli matrices of add_sigma_h).
-template <int K>
-__device__ __forceinline__ H6<float> sigma_h(const H6<float>& h) {
-  H6<float> o;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (K == 0) { o.v[0][a] = h.v[1][a]; o.v[1][a] = h.v[0][a]; }
-    else if (K == 1) { o.v[0][a] = tmi(h.v[1][a]); o.v[1][a] = ti(h.v[0][a]); }
-    else { o.v[0][a] = h.v[0][a]; o.v[1][a] = -h.v[1][a]; }
-  }
-  return o;
-}
-
-// x h + y g component-wise.
-__device__ __forceinline__ H6<float> lin2(float x, const H6<float>& h, float y, const H6<float>& g) {
-  H6<float> o;
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      o.v[q][k] = mk<float>(fmaf(y, g.v[q][k].re, x * h.v[q][k].re), fmaf(y, g.v[q][k].im, x * h.v[q][k].im));
-  return o;
-}
-
-template <int I, bool FWD, typename WS>
-__device__ __forceinline__ void f2_spatial(const WS& W, const cx<float>* __restrict__ psi, const int (&c)[4], const Geom& g,
-                                           int s, const Pair& pr, Acc2& a) {
-  const int base = M_WP + 8 * I;
-  H6<float> h;
-  if constexpr (FWD) {
-    gather_pair<float, I == 0, I == 1, I == 2, 0>(psi, c, g, pr, h);
-    const Bc6 b = bcast(h);
-    const int m = base + 4 * pr.p;
-    mvs<false, false>(a, 0, W(s, m + 0), b, 0);
-    mvs<false, false>(a, 0, W(s, m + 1), b, 1);
-    mvs<false, false>(a, 1, W(s, m + 2), b, 0);
-    mvs<false, false>(a, 1, W(s, m + 3), b, 1);
-  } else {
-    const int n = gather_pair<float, -(I == 0), -(I == 1), -(I == 2), 0>(psi, c, g, pr, h);
-    const Bc6 b = bcast(h);
-    const int m = base + 4 * (1 - pr.p);
-    mvs<true, false>(a, 0, W(n, m + 0), b, 0);
-    mvs<true, false>(a, 1, W(n, m + 1), b, 0);
-    mvs<true, false>(a, 0, W(n, m + 2), b, 1);
-    mvs<true, false>(a, 1, W(n, m + 3), b, 1);
-  }
-}
-
-// forward:  acc0 += sg (s3 h0 + n1 h1 - U l0),  acc1 += sg (-s3 h1 + n2 h0 - U l1)
-// backward: acc0 += -sg (s3^ h0 + n2^ h1) - U^ u0,  acc1 += -sg (-s3^ h1 + n1^ h0) - U^ u1
-template <bool FWD, typename WS>
-__device__ __forceinline__ void f2_time(const WS& W, const cx<float>* __restrict__ psi, const int (&c)[4], const Geom& g,
-                                        int s, const Pair& pr, Acc2& a) {
-  const float sg = pr.p ? -1.f : 1.f;
-  H6<float> h, x;
-  if constexpr (FWD) {
-    gather_pair<float, 0, 0, 0, 1>(psi, c, g, pr, h, nullptr, &x);
-    {
-      const Bc6 b = bcast(h, sg);
-      mvs<false, false>(a, 0, W(s, M_ST + 0), b, 0);
-      mvs<false, true>(a, 1, W(s, M_ST + 0), b, 1);
-      mvs<false, false>(a, 0, W(s, M_ST + 1), b, 1);
-      mvs<false, false>(a, 1, W(s, M_ST + 2), b, 0);
-    }
-    const Bc6 bl = bcast(x, sg);
-    const M3<float> U = W(s, M_UT);
-    mvs<false, true>(a, 0, U, bl, 0);
-    mvs<false, true>(a, 1, U, bl, 1);
-  } else {
-    const int n = gather_pair<float, 0, 0, 0, -1>(psi, c, g, pr, h, &x, nullptr);
-    {
-      const Bc6 b = bcast(h, sg);
-      const M3<float> s3 = W(n, M_ST + 0);
-      mvs<true, true>(a, 0, s3, b, 0);
-      mvs<true, false>(a, 1, s3, b, 1);
-      mvs<true, true>(a, 0, W(n, M_ST + 2), b, 1);
-      mvs<true, true>(a, 1, W(n, M_ST + 1), b, 0);
-    }
-    const Bc6 bu = bcast(x);
-    const M3<float> U = W(n, M_UT);
-    mvs<true, true>(a, 0, U, bu, 0);
-    mvs<true, true>(a, 1, U, bu, 1);
-  }
-}
-
-// W^{++}_ii: acc+- += V (a h +- b sigma_i h) forward, V^dag (a h -+ b sigma_i h) backward.
-template <int I, bool FWD, typename WS>
-__device__ __forceinline__ void f2_two(const WS& W, const cx<float>* __restrict__ psi, const int (&c)[4], const Geom& g,
-                                       int s, const Pair& pr, float av, float bv, Acc2& a) {
-  const float sb = pr.p ? -bv : bv;
-  H6<float> h;
-  int n = s;
-  if constexpr (FWD) gather_pair<float, 2 * (I == 0), 2 * (I == 1), 2 * (I == 2), 0>(psi, c, g, pr, h);
-  else n = gather_pair<float, -2 * (I == 0), -2 * (I == 1), -2 * (I == 2), 0>(psi, c, g, pr, h);
-  const Bc6 b = bcast(lin2(av, h, FWD ? sb : -sb, sigma_h<I>(h)));
-  const M3<float> V = W(n, M_VII + I);
-  mvs<!FWD, false>(a, 0, V, b, 0);
-  mvs<!FWD, false>(a, 1, V, b, 1);
-}
-
-// Diagonal pair (I, J): V (f (s_I + s_J) h) from x + I + J and X (f (s_I - s_J) h) from x + I - J,
-// f = sg forward; the adjoints from x - I - J and x - I + J with f = -sg backward.
-template <int I, int J, int P, bool FWD, typename WS>
-__device__ __forceinline__ void f2_diag(const WS& W, const cx<float>* __restrict__ psi, const int (&c)[4], const Geom& g,
-                                        int s, const Pair& pr, Acc2& a) {
-  constexpr int A0 = (I == 0) + (J == 0), A1 = (I == 1) + (J == 1), A2 = (I == 2) + (J == 2);
-  constexpr int B0 = (I == 0) - (J == 0), B1 = (I == 1) - (J == 1), B2 = (I == 2) - (J == 2);
-  const float sg = pr.p ? -1.f : 1.f;
-  const float f = FWD ? sg : -sg;
-  H6<float> h;
-  int n = s;
-  if constexpr (FWD) gather_pair<float, A0, A1, A2, 0>(psi, c, g, pr, h);
-  else n = gather_pair<float, -A0, -A1, -A2, 0>(psi, c, g, pr, h);
-  {
-    const Bc6 b = bcast(lin2(f, sigma_h<I>(h), f, sigma_h<J>(h)));
-    const M3<float> V = W(n, M_VIJ + P);
-    mvs<!FWD, false>(a, 0, V, b, 0);
-    mvs<!FWD, false>(a, 1, V, b, 1);
-  }
-  if constexpr (FWD) gather_pair<float, B0, B1, B2, 0>(psi, c, g, pr, h);
-  else n = gather_pair<float, -B0, -B1, -B2, 0>(psi, c, g, pr, h);
-  const Bc6 b = bcast(lin2(f, sigma_h<I>(h), -f, sigma_h<J>(h)));
-  const M3<float> X = W(n, M_XIJ + P);
-  mvs<!FWD, false>(a, 0, X, b, 0);
-  mvs<!FWD, false>(a, 1, X, b, 1);
-}
-
 }  // namespace okgb
