@@ -90,11 +90,10 @@ int ok_precompute_W(const ok_lattice* lat, const void* links, ok_prec links_prec
 
 void ok_free_W(ok_W* W) {
   if (!W) return;
-  if (W->W64) cudaFree(W->W64);
-  if (W->W32) cudaFree(W->W32);
-  if (W->Wdf) cudaFree(W->Wdf);
-  if (W->W16) cudaFree(W->W16);
-  if (W->L32) cudaFree(W->L32);
+  // Returned to the stream-ordered pool they came from, after the work already queued on the
+  // legacy default stream (the caller guarantees that no work on the handle is pending).
+  for (void* q : {W->W64, W->W32, W->Wdf, W->W16, W->L32})
+    if (q) cudaFreeAsync(q, 0);
   delete W;
 }
 

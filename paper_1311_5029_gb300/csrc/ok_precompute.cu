@@ -523,6 +523,24 @@ __global__ void links_blocked_kernel(const cx<T>* __restrict__ in, cx<float>* __
   out[(((size_t)(site >> 5) * 4 + mu) * 9 + e) * LANES + (site & 31)] = mk<float>((float)u.re, (float)u.im);
 }
 
+// The handle's arrays come from the device's default stream-ordered memory pool.  Let the pool
+// keep up to 8 GiB of freed memory (instead of returning it at every synchronisation), so that a
+// caller that builds and frees a handle per gauge field does not pay for mapping it each time.
+// Raised once per device, and only if the pool is at its default of 0.
+static void keep_pool_memory() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  static bool done[64] = {};
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  done[dev] = true;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+  unsigned long long thr = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr) != cudaSuccess || thr != 0) return;
+  thr = 8ULL << 30;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+}
+
 int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, const ok_coeffs* c,
                int precs, cudaStream_t st, ok_W** W_out) {
   if (!lat || !links || !c || !W_out) return OK_EINVAL;
@@ -541,50 +559,48 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
   W->precs = precs;
   OK_CUDA_TRY(cudaGetDevice(&W->device));
   size_t elems = (size_t)g.nblk * SITE_ELEMS * LANES;
+  // Stream-ordered allocations (cheap when the pool already holds the memory, e.g. one handle per
+  // step); only the last site block, whose lanes past V are never written, is cleared.
+  const size_t tail = (size_t)(g.nblk - 1) * SITE_ELEMS * LANES;
+  keep_pool_memory();
   int rc = OK_SUCCESS;
   cx<double>* EB = nullptr;
   double* part = nullptr;
   WScalars* dsc = nullptr;
   auto fail = [&](int code) {
-    if (EB) cudaFree(EB);
-    if (part) cudaFree(part);
-    if (dsc) cudaFree(dsc);
-    if (W->W64) cudaFree(W->W64);
-    if (W->W32) cudaFree(W->W32);
-    if (W->Wdf) cudaFree(W->Wdf);
-    if (W->W16) cudaFree(W->W16);
-    if (W->L32) cudaFree(W->L32);
+    for (void* q : {(void*)EB, (void*)part, (void*)dsc, W->W64, W->W32, W->Wdf, W->W16, W->L32})
+      if (q) cudaFreeAsync(q, st);
     delete W;
     return code;
   };
   cudaError_t e;
   if (precs & OK_W_F64) {
-    e = cudaMalloc(&W->W64, elems * sizeof(cx<double>));
+    e = cudaMallocAsync(&W->W64, elems * sizeof(cx<double>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
-    e = cudaMemsetAsync(W->W64, 0, elems * sizeof(cx<double>), st);
+    e = cudaMemsetAsync(static_cast<cx<double>*>(W->W64) + tail, 0, (elems - tail) * sizeof(cx<double>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
   }
   if (precs & OK_W_F32) {
-    e = cudaMalloc(&W->W32, elems * sizeof(cx<float>));
+    e = cudaMallocAsync(&W->W32, elems * sizeof(cx<float>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
-    e = cudaMemsetAsync(W->W32, 0, elems * sizeof(cx<float>), st);
+    e = cudaMemsetAsync(static_cast<cx<float>*>(W->W32) + tail, 0, (elems - tail) * sizeof(cx<float>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
   }
   if (precs & OK_W_DF64) {
-    e = cudaMalloc(&W->Wdf, elems * sizeof(cx<dd>));
+    e = cudaMallocAsync(&W->Wdf, elems * sizeof(cx<dd>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
-    e = cudaMemsetAsync(W->Wdf, 0, elems * sizeof(cx<dd>), st);
+    e = cudaMemsetAsync(static_cast<cx<dd>*>(W->Wdf) + tail, 0, (elems - tail) * sizeof(cx<dd>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
   }
   if (precs & OK_W_F16) {
-    e = cudaMalloc(&W->W16, elems * sizeof(cx<__half>));
+    e = cudaMallocAsync(&W->W16, elems * sizeof(cx<__half>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
-    e = cudaMemsetAsync(W->W16, 0, elems * sizeof(cx<__half>), st);
+    e = cudaMemsetAsync(static_cast<cx<__half>*>(W->W16) + tail, 0, (elems - tail) * sizeof(cx<__half>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
   }
   const size_t nlink = (size_t)g.nblk * LANES * 4 * 9;  // blocked: whole 32-site blocks
   if (precs & OK_W_LINKS) {
-    e = cudaMalloc(&W->L32, nlink * sizeof(cx<float>));
+    e = cudaMallocAsync(&W->L32, nlink * sizeof(cx<float>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
     e = cudaMemsetAsync(W->L32, 0, nlink * sizeof(cx<float>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
@@ -601,11 +617,11 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
              (W->Wdf ? elems * sizeof(cx<dd>) : 0) + (W->W16 ? elems * sizeof(cx<__half>) : 0) +
              (W->L32 ? nlink * sizeof(cx<float>) : 0);
   int nb1 = grid_for(g.V, K1_THREADS);
-  e = cudaMalloc(&EB, (size_t)g.V * 6 * 9 * sizeof(cx<double>));
+  e = cudaMallocAsync((void**)&EB, (size_t)g.V * 6 * 9 * sizeof(cx<double>), st);
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
-  e = cudaMalloc(&part, (size_t)nb1 * sizeof(double));
+  e = cudaMallocAsync((void**)&part, (size_t)nb1 * sizeof(double), st);
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
-  e = cudaMalloc(&dsc, sizeof(WScalars));
+  e = cudaMallocAsync((void**)&dsc, sizeof(WScalars), st);
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
   rc = links_prec == OK_F64 ? run_precompute<double>(W, links, c, st, EB, part, dsc)
                             : run_precompute<float>(W, links, c, st, EB, part, dsc);
@@ -614,9 +630,9 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
-  cudaFree(EB);
-  cudaFree(part);
-  cudaFree(dsc);
+  cudaFreeAsync(EB, st);
+  cudaFreeAsync(part, st);
+  cudaFreeAsync(dsc, st);
   EB = nullptr; part = nullptr; dsc = nullptr;
   *W_out = W;
   return OK_SUCCESS;
