@@ -116,8 +116,10 @@ typedef struct ok_net ok_net;  /* opaque, library-owned learned preconditioner (
 int ok_precompute_W(const ok_lattice* lat, const void* links, ok_prec links_prec,
                     const ok_coeffs* coeffs, int W_precs, void* stream, ok_W** W_out);
 
-/* Release a handle from ok_precompute_W (NULL is ignored).  Frees device memory; call it only
- * after work using the handle has completed. */
+/* Release a handle from ok_precompute_W (NULL is ignored).  Its arrays return to the device's
+ * stream-ordered memory pool (ordered on the legacy default stream); call it only after work using
+ * the handle has completed.  ok_precompute_W lets that pool keep up to 8 GiB of released memory
+ * (if the pool's release threshold was still 0), so the next handle reuses it without mapping. */
 void ok_free_W(ok_W* W);
 
 /* u0 used by the handle (given or computed from the mean plaquette); NaN if W is NULL. */
