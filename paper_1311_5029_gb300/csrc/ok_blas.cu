@@ -9,6 +9,10 @@
 // st[blockIdx.y] and its own reduction partials (one launch for all systems of a multi-RHS solve).
 #include "ok_launch.cuh"
 
+#include <mutex>
+#include <utility>
+#include <vector>
+
 namespace okgb {
 
 constexpr int BLAS_THREADS = 256;
@@ -217,9 +221,35 @@ int sm_count() {
   return g_sms;
 }
 
+// Upper bound of every vector kernel's grid width (sizes the reduction partials).
 int blas_blocks(long long units) {
   long long need = (units + BLAS_THREADS - 1) / BLAS_THREADS;
   long long cap = (long long)sm_count() * 8;
+  return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
+// Grid width for one vector kernel: one full wave of the blocks that fit on the device at once
+// (from the occupancy calculator; a grid-stride loop covers the rest).  A wider grid would leave a
+// partial second wave that every thread of the first must wait for: the kernels that hold more
+// registers (update_xr at 48) fit 5 blocks of 256 threads per SM, not 8.
+template <typename K>
+static int wave_blocks(K kern, long long units) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> cache;
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (const auto& e : cache)
+      if (e.first == (const void*)kern) per_sm = e.second;
+    if (per_sm == 0) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLAS_THREADS, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+      if (per_sm > 8) per_sm = 8;
+      cache.emplace_back((const void*)kern, per_sm);
+    }
+  }
+  const long long need = (units + BLAS_THREADS - 1) / BLAS_THREADS;
+  const long long cap = (long long)sm_count() * per_sm;
   return (int)(need < cap ? (need > 0 ? need : 1) : cap);
 }
 
@@ -231,7 +261,7 @@ int launch_update_s(const cx<R>* r, const cx<R>* v, cx<R>* s, long long n, const
   long long nu = units_of<R>(n);
   {
     TraceScope ts(sizeof(R) == 8 ? "update_s_f64" : "update_s_f32", strm);
-    update_s_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((const T*)r, (const T*)v, (T*)s, nu, st);
+    update_s_kernel<R><<<wave_blocks(update_s_kernel<R>, nu), BLAS_THREADS, 0, strm>>>((const T*)r, (const T*)v, (T*)s, nu, st);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
@@ -245,7 +275,7 @@ int launch_update_xr(cx<R>* x, const cx<R>* p, const cx<R>* s, const cx<R>* t, c
   RedArgs ra{st, part, nullptr, FIN_XR};
   {
     TraceScope ts(sizeof(R) == 8 ? "update_xr_f64" : "update_xr_f32", strm);
-    update_xr_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r,
+    update_xr_kernel<R><<<wave_blocks(update_xr_kernel<R>, nu), BLAS_THREADS, 0, strm>>>((T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r,
                                                                   (const T*)rhat, nu, st, ra, 0, (const T*)sx);
   }
   OK_LAUNCH_CHECK();
@@ -258,7 +288,7 @@ int launch_update_p(cx<R>* p, const cx<R>* r, const cx<R>* v, long long n, const
   long long nu = units_of<R>(n);
   {
     TraceScope ts(sizeof(R) == 8 ? "update_p_f64" : "update_p_f32", strm);
-    update_p_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((T*)p, (const T*)r, (const T*)v, nu, st);
+    update_p_kernel<R><<<wave_blocks(update_p_kernel<R>, nu), BLAS_THREADS, 0, strm>>>((T*)p, (const T*)r, (const T*)v, nu, st);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
@@ -271,7 +301,7 @@ int launch_restart(const cx<R>* r, cx<R>* rhat, cx<R>* p, long long n, SolverSta
   RedArgs ra{st, part, nullptr, FIN_RESTART};
   {
     TraceScope ts(sizeof(R) == 8 ? "restart_f64" : "restart_f32", strm);
-    restart_kernel<R><<<blas_blocks(nu), BLAS_THREADS, 0, strm>>>((const T*)r, (T*)rhat, (T*)p, nu, st, ra);
+    restart_kernel<R><<<wave_blocks(restart_kernel<R>, nu), BLAS_THREADS, 0, strm>>>((const T*)r, (T*)rhat, (T*)p, nu, st, ra);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
@@ -285,7 +315,7 @@ int launch_update_s_multi(const cx<float>* r, const cx<float>* v, cx<float>* s, 
   const long long nu = units_of<float>(n);
   {
     TraceScope ts("update_s_multi", strm);
-    update_s_kernel<float><<<dim3(blas_blocks(nu), nrhs), BLAS_THREADS, 0, strm>>>((const T*)r, (const T*)v, (T*)s, nu, st);
+    update_s_kernel<float><<<dim3(wave_blocks(update_s_kernel<float>, nu), nrhs), BLAS_THREADS, 0, strm>>>((const T*)r, (const T*)v, (T*)s, nu, st);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
@@ -300,7 +330,7 @@ int launch_update_xr_multi(cx<float>* x, const cx<float>* p, const cx<float>* s,
   RedArgs ra{st, part, nullptr, FIN_XR};
   {
     TraceScope ts("update_xr_multi", strm);
-    update_xr_kernel<float><<<dim3(blas_blocks(nu), nrhs), BLAS_THREADS, 0, strm>>>(
+    update_xr_kernel<float><<<dim3(wave_blocks(update_xr_kernel<float>, nu), nrhs), BLAS_THREADS, 0, strm>>>(
         (T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r, (const T*)rhat, nu, st, ra, pstride, (const T*)sx);
   }
   OK_LAUNCH_CHECK();
@@ -313,7 +343,7 @@ int launch_update_p_multi(cx<float>* p, const cx<float>* r, const cx<float>* v, 
   const long long nu = units_of<float>(n);
   {
     TraceScope ts("update_p_multi", strm);
-    update_p_kernel<float><<<dim3(blas_blocks(nu), nrhs), BLAS_THREADS, 0, strm>>>((T*)p, (const T*)r, (const T*)v, nu, st);
+    update_p_kernel<float><<<dim3(wave_blocks(update_p_kernel<float>, nu), nrhs), BLAS_THREADS, 0, strm>>>((T*)p, (const T*)r, (const T*)v, nu, st);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
@@ -321,14 +351,15 @@ int launch_update_p_multi(cx<float>* p, const cx<float>* r, const cx<float>* v, 
 
 int launch_demote(const cx<double>* r64, cx<float>* r32, cx<float>* rhat, cx<float>* p, long long n, bool restart,
                   SolverState* st, double* part, cudaStream_t strm) {
-  int nb = blas_blocks(n);
   if (restart) {
+    const int nb = wave_blocks(demote_kernel<true>, n);
     RedArgs ra{st, part, nullptr, FIN_RESTART};
     {
     TraceScope ts("demote_restart", strm);
     demote_kernel<true><<<nb, BLAS_THREADS, 0, strm>>>((const double2*)r64, (float2*)r32, (float2*)rhat, (float2*)p, n, st, ra);
   }
   } else {
+    const int nb = wave_blocks(demote_kernel<false>, n);
     RedArgs ra{st, part, nullptr, FIN_CONTINUE};
     {
     TraceScope ts("demote_continue", strm);
@@ -342,7 +373,7 @@ int launch_demote(const cx<double>* r64, cx<float>* r32, cx<float>* rhat, cx<flo
 int launch_accum_x(cx<double>* x64, cx<float>* x32, long long n, cudaStream_t strm) {
   {
     TraceScope ts("accum_x", strm);
-    accum_x_kernel<<<blas_blocks(n), BLAS_THREADS, 0, strm>>>((double2*)x64, (float2*)x32, n);
+    accum_x_kernel<<<wave_blocks(accum_x_kernel, n), BLAS_THREADS, 0, strm>>>((double2*)x64, (float2*)x32, n);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
@@ -351,7 +382,7 @@ int launch_accum_x(cx<double>* x64, cx<float>* x32, long long n, cudaStream_t st
 int launch_to_df(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t strm) {
   {
     TraceScope ts("to_df64", strm);
-    to_df_kernel<<<blas_blocks(n), BLAS_THREADS, 0, strm>>>((const double2*)in, (float4*)out, n);
+    to_df_kernel<<<wave_blocks(to_df_kernel, n), BLAS_THREADS, 0, strm>>>((const double2*)in, (float4*)out, n);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
@@ -361,7 +392,7 @@ int launch_norms(const cx<double>* x, const cx<double>* b, long long n, SolverSt
   RedArgs ra{st, part, nullptr, FIN_RESID};
   {
     TraceScope ts("norms_f64", strm);
-    norms_kernel<<<blas_blocks(n), BLAS_THREADS, 0, strm>>>((const double2*)x, (const double2*)b, n, st, ra);
+    norms_kernel<<<wave_blocks(norms_kernel, n), BLAS_THREADS, 0, strm>>>((const double2*)x, (const double2*)b, n, st, ra);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
