@@ -16,6 +16,7 @@
 //             final sum over the blocks (deterministic).
 //   loss:     |P b - x|^2 / |x|^2 per pair with the seed g_K = (P b - x) / |x|^2.
 //   Adam:     on the real and imaginary parts of every A entry.
+#include "ok_net.cuh"
 #include "ok_pair.cuh"
 
 #include <cmath>
@@ -114,11 +115,13 @@ __device__ __forceinline__ void transported(const cx<float>* __restrict__ L, con
 
 // out = sum_d A_d T_d in   (ADJ: sum_d A_d^dag T_{-d} in, the adjoint layer).  With nrhs fields
 // [nrhs][V][12] per launch, block b works on field b % nrhs and site block b / nrhs, so the blocks
-// that read the same links run back to back and share them through L2.
+// that read the same links run back to back and share them through L2.  With `halt` non-null and
+// nonzero at launch the kernel does nothing.
 template <bool ADJ>
 __global__ void __launch_bounds__(NET_THREADS) net_layer_kernel(const cx<float>* __restrict__ L, const float2* __restrict__ A,
                                                                 const cx<float>* __restrict__ in, cx<float>* __restrict__ out,
-                                                                Geom g, int nrhs) {
+                                                                Geom g, int nrhs, const int* __restrict__ halt) {
+  if (halt && *halt) return;  // a halted solver state: this layer belongs to an iteration that does nothing
   const int rhs = blockIdx.x % nrhs, sb = blockIdx.x / nrhs;
   in += (size_t)rhs * 12 * g.V;
   out += (size_t)rhs * 12 * g.V;
@@ -299,16 +302,16 @@ int ensure_workspace(ok_net* N, int V, bool training) {
 }
 
 int layer(const ok_net* N, const ok_W* W, int l, bool adj, const cx<float>* in, cx<float>* out, cudaStream_t st,
-          int nrhs = 1) {
+          int nrhs = 1, const int* halt = nullptr) {
   const Geom& g = W->g;
   const long long nb = (long long)grid_for(g.V, NET_THREADS) * nrhs;
   if (nb > 0x7fffffffLL) return OK_EINVAL;
   {
     TraceScope ts(adj ? "net_layer_adj" : "net_layer", st);
     if (adj)
-      net_layer_kernel<true><<<(unsigned)nb, NET_THREADS, 0, st>>>((const cx<float>*)W->L32, N->A + (size_t)l * 144, in, out, g, nrhs);
+      net_layer_kernel<true><<<(unsigned)nb, NET_THREADS, 0, st>>>((const cx<float>*)W->L32, N->A + (size_t)l * 144, in, out, g, nrhs, halt);
     else
-      net_layer_kernel<false><<<(unsigned)nb, NET_THREADS, 0, st>>>((const cx<float>*)W->L32, N->A + (size_t)l * 144, in, out, g, nrhs);
+      net_layer_kernel<false><<<(unsigned)nb, NET_THREADS, 0, st>>>((const cx<float>*)W->L32, N->A + (size_t)l * 144, in, out, g, nrhs, halt);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
@@ -372,16 +375,21 @@ int check(const ok_net* N, const ok_W* W) {
 
 }  // namespace
 
-int net_apply(ok_net* N, const ok_W* W, const cx<float>* in, cx<float>* out, cudaStream_t st) {
+int net_apply_unless_halted(ok_net* N, const ok_W* W, const cx<float>* in, cx<float>* out, const int* halt,
+                           cudaStream_t st) {
   NET_TRY(check(N, W));
   NET_TRY(ensure_workspace(N, W->g.V, false));
   const cx<float>* cur = in;
   for (int l = 0; l < N->layers; ++l) {
     cx<float>* o = l == N->layers - 1 ? out : N->g[l % 2];  // ping-pong through the workspace
-    NET_TRY(layer(N, W, l, false, cur, o, st));
+    NET_TRY(layer(N, W, l, false, cur, o, st, 1, halt));
     cur = o;
   }
   return OK_SUCCESS;
+}
+
+int net_apply(ok_net* N, const ok_W* W, const cx<float>* in, cx<float>* out, cudaStream_t st) {
+  return net_apply_unless_halted(N, W, in, out, nullptr, st);
 }
 
 // out_k = P in_k for nrhs fields [nrhs][V][12] in one launch per layer, through the caller's two

@@ -6,8 +6,8 @@
 //   t = M s            (apply, fused <t, s>, <t, t>  -> omega)
 //   x += alpha p + omega s,  r = s - omega t  (fused <rhat, r>, <r, r> -> beta, convergence)
 //   p = r + beta (p - omega v)
-// The host enqueues `check_every` iterations at a time and then reads the state once; kernels
-// enqueued after the state halted do nothing.
+// The host enqueues `check_every` iterations at a time and then reads the state once, with one
+// more iteration enqueued behind the read; kernels enqueued after the state halted do nothing.
 //
 // Plain mode: everything FP64.  On convergence of the iterated residual, the true residual
 // b - M x is recomputed; if it is still above tol the method restarts from it (also after a
@@ -20,6 +20,7 @@
 // direction (Sleijpen and van der Vorst, "Reliable updated residuals in hybrid Bi-CG methods",
 // Computing 56 (1996) 141).  The iteration stops when the FP64 true residual is below tol.
 #include "ok_launch.cuh"
+#include "ok_net.cuh"
 
 #include <chrono>
 #include <cmath>
@@ -95,6 +96,14 @@ struct Precond {
   ok_net* net = nullptr;
   cx<float>* zp = nullptr;  // P p
   cx<float>* zs = nullptr;  // P s
+  const int* halt = nullptr;  // the solver state's halt flag: no network work once it is set
+};
+
+// A timing-free CUDA event owned for the scope.
+struct Event {
+  cudaEvent_t e = nullptr;
+  ~Event() { if (e) cudaEventDestroy(e); }
+  cudaError_t create() { return cudaEventCreateWithFlags(&e, cudaEventDisableTiming); }
 };
 
 // One BiCGStab iteration.  With a right preconditioner P the operator is M P:  v = M (P p),
@@ -109,7 +118,7 @@ int iterate(const ok_W* W, const IterBufs<R>& b, long long n, SolverState* dst, 
   if constexpr (sizeof(R) == 4) {
     if (pc.net) {
       pre = true;
-      OK_TRY(net_apply(pc.net, W, b.p, pc.zp, st));
+      OK_TRY(net_apply_unless_halted(pc.net, W, b.p, pc.zp, pc.halt, st));
       pin = pc.zp;
     }
   }
@@ -118,7 +127,7 @@ int iterate(const ok_W* W, const IterBufs<R>& b, long long n, SolverState* dst, 
   OK_TRY(launch_update_s<R>(b.r, b.v, b.s, n, dst, st));
   if constexpr (sizeof(R) == 4) {
     if (pre) {
-      OK_TRY(net_apply(pc.net, W, b.s, pc.zs, st));
+      OK_TRY(net_apply_unless_halted(pc.net, W, b.s, pc.zs, pc.halt, st));
       sin = pc.zs;
     }
   }
@@ -217,10 +226,12 @@ int bicgstab_impl(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok
     pc.net = net;
     pc.zp = ws.get<cx<float>>(n, &err);
     pc.zs = ws.get<cx<float>>(n, &err);
+    pc.halt = &dst->halt;
     if (!pc.zp || !pc.zs) { set_cuda_error(err); return OK_ENOMEM; }
   }
 
   auto finish = [&](int rc, double rr_true) {
+    cudaStreamSynchronize(st);  // the iteration enqueued ahead of the last check (it does nothing)
     inf.true_relres = h->bb > 0.0 ? sqrt(rr_true / h->bb) : sqrt(rr_true);
     inf.iter_relres = h->bb > 0.0 ? sqrt(h->rr / h->bb) : sqrt(h->rr);
     inf.iters = h->iter;
@@ -252,14 +263,30 @@ int bicgstab_impl(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok
   }
   if (h->rr < h->tol2 * h->bb) return finish(OK_SUCCESS, rr_true);
 
-  for (;;) {
-    for (int k = 0; k < prm->check_every; ++k) {
+  // Blocks of check_every iterations with a state read after each.  The read overlaps one more
+  // iteration, which the host enqueues before it waits for the read, so that the GPU does not idle
+  // through the host's round trip; when the read shows a halt, every kernel of that iteration finds
+  // the halt flag set and does nothing, and the state stays as read.
+  auto enqueue = [&](int iters) -> int {
+    for (int k = 0; k < iters; ++k) {
       if (mode == OK_SOLVE_F64) OK_TRY(iterate<double>(W, b64, n, dst, part, false, Precond{}, st));
       else OK_TRY(iterate<float>(W, b32, n, dst, part, w16, pc, st));
     }
-    OK_TRY(read_state(dst, h, st));
+    return OK_SUCCESS;
+  };
+  Event snap;
+  OK_CUDA_TRY(snap.create());
+  OK_TRY(enqueue(prm->check_every));
+  for (;;) {
+    OK_CUDA_TRY(cudaMemcpyAsync(h, dst, sizeof(SolverState), cudaMemcpyDeviceToHost, st));
+    OK_CUDA_TRY(cudaEventRecord(snap.e, st));
+    OK_TRY(enqueue(1));
+    OK_CUDA_TRY(cudaEventSynchronize(snap.e));
     int halt = h->halt;
-    if (halt == HALT_NONE) continue;
+    if (halt == HALT_NONE) {
+      OK_TRY(enqueue(prm->check_every - 1));
+      continue;
+    }
     if (halt == HALT_NONFINITE) return finish(OK_ENONFINITE, rr_true);
     // true residual
     if (mode == OK_SOLVE_MIXED) OK_TRY(launch_accum_x(x, b32.x, n, st));
@@ -275,6 +302,7 @@ int bicgstab_impl(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok
       inf.reliable_updates++;
       OK_TRY(launch_demote(r64, b32.r, b32.rhat, b32.p, n, false, dst, part, st));
       OK_TRY(launch_update_p<float>(b32.p, b32.r, b32.v, n, dst, st));
+      OK_TRY(enqueue(prm->check_every));
       continue;
     }
     // converged iterated residual that the true residual does not confirm, or a breakdown:
@@ -284,6 +312,7 @@ int bicgstab_impl(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok
     inf.restarts++;
     if (mode == OK_SOLVE_F64) OK_TRY(launch_restart<double>(r64, b64.rhat, b64.p, n, dst, part, st));
     else OK_TRY(launch_demote(r64, b32.r, b32.rhat, b32.p, n, true, dst, part, st));
+    OK_TRY(enqueue(prm->check_every));
   }
 }
 

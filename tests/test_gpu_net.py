@@ -71,6 +71,24 @@ def test_identity_network_leaves_the_solve_unchanged():
     assert r < 1e-10
 
 
+def test_preconditioned_solve_is_independent_of_the_check_cadence():
+    """The network's layers, like the other kernels of an iteration enqueued after the state
+    halted, change nothing: the preconditioned solve is bit-identical for any check_every."""
+    dims, bc = (6, 4, 4, 6), (1, 1, 1, 1)
+    U = synth.random_links(dims, 0.3, 9721)
+    c = synth.placeholder_coeffs(0.5)
+    W = ok.precompute_W(to_dev(U), c, bc, ok.W_F64 | ok.W_F32 | ok.W_LINKS)
+    b = to_dev(synth.gaussian_source(dims, 9722))
+    net = ok.Net(2, _weights(2, 9723, 0.05))
+    runs = [ok.bicgstab_net(W, net, b, tol=1e-10, mode=ok.SOLVE_MIXED, delta=1e-2, check_every=ce) for ce in (1, 4, 7)]
+    x0, i0 = runs[0]
+    assert i0["status"] == 0
+    r = np.linalg.norm(b.cpu().numpy() - wform.apply(U, c, x0.cpu().numpy(), bc)) / np.linalg.norm(b.cpu().numpy())
+    assert r < 1e-10
+    for x, i in runs[1:]:
+        assert torch.equal(x, x0) and i["iters"] == i0["iters"]
+
+
 def test_training_lowers_the_loss_and_the_trained_preconditioner_solves():
     """Train on pairs from our own solver over three synthetic fields, then solve a held-out field."""
     dims, bc = (8, 8, 8, 8), (1, 1, 1, 1)

@@ -108,6 +108,22 @@ def test_solves_are_deterministic():
         assert torch.equal(xa, xb) and ia["iters"] == ib["iters"]
 
 
+def test_check_cadence_does_not_change_the_solve():
+    """Kernels enqueued after the state halted (the rest of a block, and the iteration enqueued
+    behind each state read) do nothing: the solve is bit-identical for any check_every."""
+    dims = (6, 4, 4, 6)
+    U = synth.random_links(dims, 0.3, 9501)
+    W = ok.precompute_W(to_dev(U), synth.placeholder_coeffs(0.5), (1, 1, 1, 1), ok.W_F64 | ok.W_F32)
+    b = to_dev(synth.gaussian_source(dims, 9502))
+    for mode, delta in ((ok.SOLVE_F64, 1e-2), (ok.SOLVE_MIXED, 1e-2)):
+        runs = [ok.bicgstab(W, b, tol=TOL, mode=mode, delta=delta, check_every=ce) for ce in (1, 3, 8)]
+        x0, i0 = runs[0]
+        assert i0["status"] == 0 and i0["true_relres"] < TOL
+        for x, i in runs[1:]:
+            assert torch.equal(x, x0)
+            assert (i["iters"], i["reliable_updates"], i["restarts"]) == (i0["iters"], i0["reliable_updates"], i0["restarts"])
+
+
 def test_mixed_solve_with_double_float_residuals():
     """FP32 iteration with reliable updates whose true residuals use the double-float FP64 copy."""
     dims, U, c, b = synth.workload_inputs("16^3x32")
