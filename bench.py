@@ -3,9 +3,10 @@
 
 A step is one pass of the whole path over the 16^3 x 32 workload (random SU(3) links, eps 0.2,
 am0 0.5, Gaussian source), with inputs resident in HBM:
-  precompute W from the links (mean plaquette / u0, clover, W matrices; FP64 and FP32 copies),
-  BiCGStab solve of M x = b to a true FP64 residual |b - M x| / |b| < 1e-10 (FP32 iteration with
-  FP64 reliable updates), release of W.
+  precompute W from the links (mean plaquette / u0, clover, W matrices; an FP64-accurate
+  double-float copy and an FP32 copy), BiCGStab solve of M x = b to a true FP64 residual
+  |b - M x| / |b| < 1e-10 (FP32 iteration with reliable updates whose FP64-accurate residuals run
+  in double-float arithmetic on the FP32 pipes), release of W.
 `value` is the step's algorithmic HBM traffic (bytes each kernel must move once) divided by the
 step time, in GB/s.  `roofline` describes the dominant kernel (the FP32 application of M inside
 the solve) timed with CUDA events on its own stream during the timed steps.  `e2e` repeats the
@@ -43,13 +44,19 @@ CHECK_EVERY = 4
 
 # Algorithmic bytes per site (each stored byte read once, each output written once).
 W64_BYTES = 43 * 9 * 16          # stored FP64 W per site
+WDF_BYTES = 43 * 9 * 32          # stored double-float W per site (two floats per FP64 component)
 W32_BYTES = 43 * 9 * 8           # stored FP32 W per site
 SPINOR64, SPINOR32 = 192, 96
+SPINORDF = 12 * 32               # double-float spinor
 LINKS64 = 4 * 9 * 16
 APPLY64 = W64_BYTES + 2 * SPINOR64            # 6576: W + psi in + out
 APPLY32 = W32_BYTES + 2 * SPINOR32            # 3288
 RESID64 = APPLY64 + SPINOR64                  # true residual also reads b
-PRECOMPUTE = LINKS64 + W64_BYTES + W32_BYTES  # links in, both W copies out
+# The mixed solve's FP64 true residual runs on the double-float copy: x is converted first (x in,
+# x_df out), then W_df + x_df + b are read and r written.
+RESIDDF = (SPINOR64 + SPINORDF) + WDF_BYTES + SPINORDF + 2 * SPINOR64
+PRECOMPUTE = {"mixed": LINKS64 + WDF_BYTES + W32_BYTES,  # links in, the two W copies out
+              "f64": LINKS64 + W64_BYTES}
 # FP32 vector traffic per BiCGStab iteration: <rhat, v> reads rhat (1); s = r - a v (3);
 # x += a p + w s, r = s - w t with two dots (5 reads + 2 writes); p = r + b (p - w v) (4).
 ITER_VEC32 = (1 + 3 + 7 + 4) * SPINOR32
@@ -65,7 +72,7 @@ def solve_bytes(V, info, mode):
     it = info["iters"]
     if mode == "mixed":
         per_iter = 2 * APPLY32 + ITER_VEC32
-        extra = info["fp64_applies"] * RESID64 + (info["reliable_updates"] + info["restarts"] + 1) * RELIABLE32
+        extra = info["fp64_applies"] * RESIDDF + (info["reliable_updates"] + info["restarts"] + 1) * RELIABLE32
     else:
         per_iter = 2 * APPLY64 + ITER_VEC64
         extra = info["fp64_applies"] * RESID64 + (info["restarts"] + 1) * RESTART64
@@ -232,7 +239,7 @@ def run_ours(args):
     bc = (1, 1, 1, 1)
     U_d = torch.from_numpy(U).to(dev)
     b_d = torch.from_numpy(b).to(dev)
-    precs = ok.W_F64 | (ok.W_F32 if args.mode == "mixed" else 0)
+    precs = (ok.W_DF64 | ok.W_F32) if args.mode == "mixed" else ok.W_F64
     mode = ok.SOLVE_MIXED if args.mode == "mixed" else ok.SOLVE_F64
 
     def step(links, src):
@@ -273,7 +280,7 @@ def run_ours(args):
     for _ in range(args.steps):
         _, info = step(U_d, b_d)
         infos.append(info)
-        tot_bytes += V * PRECOMPUTE + solve_bytes(V, info, args.mode)
+        tot_bytes += V * PRECOMPUTE[args.mode] + solve_bytes(V, info, args.mode)
     e1.record()
     torch.cuda.synchronize()
     barrier()
@@ -319,7 +326,7 @@ def run_ours(args):
             b_e.copy_(b_h, non_blocking=True)
             x, info = step(U_e, b_e)
             x_h.copy_(x, non_blocking=True)
-            e2e_bytes += V * PRECOMPUTE + solve_bytes(V, info, args.mode)
+            e2e_bytes += V * PRECOMPUTE[args.mode] + solve_bytes(V, info, args.mode)
         f1.record()
         torch.cuda.synchronize()
         barrier()
@@ -341,13 +348,15 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+df64" if args.mode == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice_xyzt": list(dims), "sites": V, "links_eps": 0.2, "am0": 0.5,
                    "source": "gaussian", "tol": TOL,
                    "solver": (f"BiCGStab FP32 + FP64 reliable updates (delta {DELTA})" if args.mode == "mixed"
                              else "BiCGStab FP64"),
-                   "step": "precompute W (FP64+FP32) + solve to 1e-10 true residual + free W",
-                   "l2": "inputs larger than L2 (W = %.2f GB per step)" % (V * (W64_BYTES + W32_BYTES) / 1e9),
+                   "step": ("precompute W (double-float FP64 + FP32) + solve to 1e-10 true residual + free W"
+                            if args.mode == "mixed" else "precompute W (FP64) + solve to 1e-10 true residual + free W"),
+                   "l2": "inputs larger than L2 (W = %.2f GB per step)" % (
+                       V * ((WDF_BYTES + W32_BYTES) if args.mode == "mixed" else W64_BYTES) / 1e9),
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "percent_of_hbm_peak": 100.0 * value / peak,

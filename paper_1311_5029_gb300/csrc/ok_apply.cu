@@ -65,41 +65,6 @@ __device__ __forceinline__ void store_spinor<float>(cx<float>* __restrict__ out,
   for (int k = 0; k < 6; ++k) p[k] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
 }
 
-// Double-float fields: input spinors are (re.hi, re.lo, im.hi, im.lo) per complex number; the
-// kernel's outputs are written as FP64 complex numbers (hi + lo rounded to double).
-template <>
-__device__ __forceinline__ void load_spinor<dd>(const cx<dd>* __restrict__ psi, int site, cx<dd> (&v)[12]) {
-  const float4* p = reinterpret_cast<const float4*>(psi) + (size_t)site * 12;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    float4 d = __ldg(p + k);
-    v[k] = mk(dd(d.x, d.y), dd(d.z, d.w));
-  }
-}
-
-template <>
-__device__ __forceinline__ void store_spinor<dd>(cx<dd>* __restrict__ out, int site, const cx<dd> (&v)[12]) {
-  double2* p = reinterpret_cast<double2*>(out) + (size_t)site * 12;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) p[k] = make_double2((double)v[k].re, (double)v[k].im);
-}
-
-// Right-hand side of the residual epilogue: FP64 for the double-float kernel, the field's own
-// precision otherwise.
-template <typename R>
-__device__ __forceinline__ void load_rhs(const cx<R>* __restrict__ b, int site, cx<R> (&v)[12]) {
-  if constexpr (std::is_same<R, dd>::value) {
-    const double2* p = reinterpret_cast<const double2*>(b) + (size_t)site * 12;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      double2 d = __ldg(p + k);
-      v[k] = mk(R(d.x), R(d.y));
-    }
-  } else {
-    load_spinor<R>(b, site, v);
-  }
-}
-
 // Gather the neighbour at offset d and form h+ = u + l, h- = u - l (with the boundary sign).
 template <typename R, int D0, int D1, int D2, int D3>
 __device__ __forceinline__ int gather_h(const cx<R>* __restrict__ psi, const int (&c)[4], const Geom& g,
@@ -356,7 +321,7 @@ __global__ void __launch_bounds__(APPLY_THREADS) apply_kernel(const cx<R>* __res
       }
     if (EPI == EPI_RESID) {
       cx<R> bv[12];
-      load_rhs<R>(ep.b, s, bv);
+      load_spinor<R>(ep.b, s, bv);
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         o[k] = bv[k] - o[k];
@@ -1001,24 +966,6 @@ int read_wait_timeouts(unsigned* n, bool reset) {
 
 // FP64-accurate application with the double-float copy of W: psi in double-float, out in FP64;
 // EPI_NONE or EPI_RESID (b in FP64).  One thread per site, as for native FP64.
-int launch_apply_df(const ok_W* Wh, const cx<dd>* psi_df, cx<double>* out, int epi, const EpiArgs<dd>& ep, cudaStream_t st) {
-  const cx<dd>* W = (const cx<dd>*)Wh->Wdf;
-  if (!W || (epi != EPI_NONE && epi != EPI_RESID)) return OK_EINVAL;
-  const Geom& g = Wh->g;
-  const dd c0q(Wh->sc.c0q), a(Wh->sc.a_ii), b(Wh->sc.b_ii);
-  const int nb = grid_for(g.V, APPLY_THREADS);
-  cx<dd>* o = reinterpret_cast<cx<dd>*>(out);  // the double-float kernel stores FP64 outputs
-  {
-    TraceScope ts(epi == EPI_RESID ? "apply_df64_resid" : "apply_df64", st);
-    if (epi == EPI_RESID)
-      apply_kernel<dd, EPI_RESID><<<nb, APPLY_THREADS, 0, st>>>(W, psi_df, o, g, c0q, a, b, ep);
-    else
-      apply_kernel<dd, EPI_NONE><<<nb, APPLY_THREADS, 0, st>>>(W, psi_df, o, g, c0q, a, b, ep);
-  }
-  OK_LAUNCH_CHECK();
-  return OK_SUCCESS;
-}
-
 template int launch_apply<double>(const ok_W*, const cx<double>*, cx<double>*, int, const EpiArgs<double>&, cudaStream_t);
 template int launch_apply<float>(const ok_W*, const cx<float>*, cx<float>*, int, const EpiArgs<float>&, cudaStream_t);
 

@@ -1,0 +1,455 @@
+// FP64-accurate M psi on the FP32 pipes: double-float W (OK_W_DF64) and fields, one thread per
+// site, the stencil walked as a table.
+//
+// The operator is the one of the other apply kernels (Eq. minFlopForm in the spin basis where
+// every hop except W^0 is block diagonal in h+- = u +- l; see ok_apply.cu): per site 27 offsets
+// and 148 colour matrix-vector products y = V h or V^dag h, each added to one or two of the four
+// accumulators acc+-(spin 0, 1) with a factor 1, a_ii or b_ii times a unit (+-1, +-i, +-1 +- i).
+// Written out with every product inlined, that is about 100 K FP32 instructions of straight-line
+// code per thread in double-float arithmetic, far beyond the instruction caches.  Here the
+// products are entries of a table in the kernel's parameter space and one compact loop body
+// executes them: the offset's neighbour spinor is gathered once into shared memory (three
+// half-spinor slots per thread), then every entry loads its matrix, multiplies and accumulates.
+// All threads of a block walk the same entries, so the table reads and the branches on an
+// entry's fields are uniform.
+//
+// Double-float: a row of a product sums six real products with TwoProd and TwoSum, deferring the
+// renormalisation to the end of the row (Joldes, Muller, Popescu, ACM TOMS 44 (2017), the
+// building blocks of ok_internal.cuh); accumulators are renormalised at every addition.
+#include "ok_dd.cuh"
+
+namespace okgb {
+
+namespace {
+
+constexpr int DD_THREADS = 128;
+#ifndef OK_DD_MINB
+#define OK_DD_MINB 4
+#endif
+
+// Table entries: sources (slot * 2 + spin), accumulators (half * 2 + spin), scalars and units.
+constexpr int HP(int q) { return q; }        // slot 0: h+ (on-site: u - i l)
+constexpr int HM(int q) { return 2 + q; }    // slot 1: h- (on-site: u + i l)
+constexpr int T3(int q) { return 4 + q; }    // slot 2: l or u of the temporal hops
+constexpr int AP(int q) { return q; }
+constexpr int AM(int q) { return 2 + q; }
+enum : int { S1 = 0, SA = 1, SB = 2 };
+enum : int { U_P1 = 0, U_PI = 1, U_M1 = 2, U_MI = 3, U_1PI = 4, U_1MI = 5, U_M1MI = 6, U_M1PI = 7 };
+constexpr int neg_unit(int u) { return u ^ 2; }
+
+// sigma_k applied to a 2-spinor with only spin q nonzero: the output spin and its unit.
+void sigma_of(int k, int q, int& qo, int& u) {
+  if (k == 0) { qo = 1 - q; u = U_P1; }
+  else if (k == 1) { qo = 1 - q; u = q == 1 ? U_MI : U_PI; }
+  else { qo = q; u = q == 0 ? U_P1 : U_M1; }
+}
+
+struct Builder {
+  DDTable t{};
+  int nh = 0, na = 0;
+  void hop(int d0, int d1, int d2, int d3, int kind) {
+    DDHop& h = t.hop[nh++];
+    h.d[0] = (signed char)d0; h.d[1] = (signed char)d1; h.d[2] = (signed char)d2; h.d[3] = (signed char)d3;
+    h.kind = (unsigned char)kind;
+    h.first = (unsigned char)na;
+    h.count = 0;
+  }
+  // y = op(W_m) (source), added to accumulator dst0 (and dst1) with scalar and unit.
+  void act(int m, bool at_nbr, bool dag, int src, int dst0, int sc0, int u0, int dst1 = -1, int sc1 = 0, int u1 = 0) {
+    DDAct& a = t.act[na++];
+    a.m = (unsigned char)m;
+    a.flags = (unsigned char)((at_nbr ? 1 : 0) | (dag ? 2 : 0) | (src << 2));
+    a.dst[0] = (signed char)dst0;
+    a.dst[1] = (signed char)dst1;
+    a.mul[0] = (unsigned char)(sc0 | (u0 << 2));
+    a.mul[1] = (unsigned char)(sc1 | (u1 << 2));
+    t.hop[nh - 1].count++;
+  }
+};
+
+// The entries follow the hop functions of ok_apply.cu term by term.
+DDTable build_table() {
+  Builder b;
+  // on-site: a = u - i l (slot 0), b = u + i l (slot 1); A = Y+ a, B = Y- b enter
+  // acc+ = (1 + i) A + (1 - i) B and acc- = (1 - i) A + (1 + i) B (the c0q part is set by the gather)
+  b.hop(0, 0, 0, 0, DD_ONSITE);
+  b.act(M_Y0P + 0, false, false, HP(0), AP(0), S1, U_1PI, AM(0), S1, U_1MI);
+  b.act(M_Y0P + 0, false, false, HP(1), AP(1), S1, U_M1MI, AM(1), S1, U_M1PI);
+  b.act(M_Y0P + 1, false, false, HP(1), AP(0), S1, U_1PI, AM(0), S1, U_1MI);
+  b.act(M_Y0P + 2, false, false, HP(0), AP(1), S1, U_1PI, AM(1), S1, U_1MI);
+  b.act(M_Y0M + 0, false, false, HM(0), AP(0), S1, U_1MI, AM(0), S1, U_1PI);
+  b.act(M_Y0M + 0, false, false, HM(1), AP(1), S1, U_M1PI, AM(1), S1, U_M1MI);
+  b.act(M_Y0M + 1, false, false, HM(1), AP(0), S1, U_1MI, AM(0), S1, U_1PI);
+  b.act(M_Y0M + 2, false, false, HM(0), AP(1), S1, U_1MI, AM(1), S1, U_1PI);
+  // spatial nearest neighbours: blocks P+ / 2 at mp .. mp + 3, P- / 2 at mm .. mm + 3
+  for (int I = 0; I < 3; ++I) {
+    const int mp = M_WP + 8 * I, mm = mp + 4;
+    b.hop(I == 0, I == 1, I == 2, 0, DD_PLAIN);
+    b.act(mp + 0, false, false, HP(0), AP(0), S1, U_P1);
+    b.act(mp + 1, false, false, HP(1), AP(0), S1, U_P1);
+    b.act(mp + 2, false, false, HP(0), AP(1), S1, U_P1);
+    b.act(mp + 3, false, false, HP(1), AP(1), S1, U_P1);
+    b.act(mm + 0, false, false, HM(0), AM(0), S1, U_P1);
+    b.act(mm + 1, false, false, HM(1), AM(0), S1, U_P1);
+    b.act(mm + 2, false, false, HM(0), AM(1), S1, U_P1);
+    b.act(mm + 3, false, false, HM(1), AM(1), S1, U_P1);
+    b.hop(-(I == 0), -(I == 1), -(I == 2), 0, DD_PLAIN);
+    b.act(mm + 0, true, true, HP(0), AP(0), S1, U_P1);
+    b.act(mm + 1, true, true, HP(0), AP(1), S1, U_P1);
+    b.act(mm + 2, true, true, HP(1), AP(0), S1, U_P1);
+    b.act(mm + 3, true, true, HP(1), AP(1), S1, U_P1);
+    b.act(mp + 0, true, true, HM(0), AM(0), S1, U_P1);
+    b.act(mp + 1, true, true, HM(0), AM(1), S1, U_P1);
+    b.act(mp + 2, true, true, HM(1), AM(0), S1, U_P1);
+    b.act(mp + 3, true, true, HM(1), AM(1), S1, U_P1);
+  }
+  // temporal: forward acc+ += S h+ - U l, acc- += U l - S h-; backward acc+ += -U^dag u - S^dag h+,
+  // acc- += -U^dag u + S^dag h-, with S = [[s3, n1], [n2, -s3]]
+  b.hop(0, 0, 0, 1, DD_THIRD_L);
+  for (int q = 0; q < 2; ++q) b.act(M_UT, false, false, T3(q), AP(q), S1, U_M1, AM(q), S1, U_P1);
+  b.act(M_ST + 0, false, false, HP(0), AP(0), S1, U_P1);
+  b.act(M_ST + 0, false, false, HP(1), AP(1), S1, U_M1);
+  b.act(M_ST + 0, false, false, HM(0), AM(0), S1, U_M1);
+  b.act(M_ST + 0, false, false, HM(1), AM(1), S1, U_P1);
+  b.act(M_ST + 1, false, false, HP(1), AP(0), S1, U_P1);
+  b.act(M_ST + 1, false, false, HM(1), AM(0), S1, U_M1);
+  b.act(M_ST + 2, false, false, HP(0), AP(1), S1, U_P1);
+  b.act(M_ST + 2, false, false, HM(0), AM(1), S1, U_M1);
+  b.hop(0, 0, 0, -1, DD_THIRD_U);
+  for (int q = 0; q < 2; ++q) b.act(M_UT, true, true, T3(q), AP(q), S1, U_M1, AM(q), S1, U_M1);
+  b.act(M_ST + 0, true, true, HP(0), AP(0), S1, U_M1);
+  b.act(M_ST + 0, true, true, HP(1), AP(1), S1, U_P1);
+  b.act(M_ST + 0, true, true, HM(0), AM(0), S1, U_P1);
+  b.act(M_ST + 0, true, true, HM(1), AM(1), S1, U_M1);
+  b.act(M_ST + 1, true, true, HP(0), AP(1), S1, U_M1);
+  b.act(M_ST + 1, true, true, HM(0), AM(1), S1, U_P1);
+  b.act(M_ST + 2, true, true, HP(1), AP(0), S1, U_M1);
+  b.act(M_ST + 2, true, true, HM(1), AM(0), S1, U_P1);
+  // straight two hops x +- 2I: (a +- b sigma_I) V h+- forward, (a -+ b sigma_I) V^dag h+- backward
+  for (int I = 0; I < 3; ++I) {
+    const int V = M_VII + I;
+    for (int dir = 0; dir < 2; ++dir) {
+      const int st = dir == 0 ? 2 : -2;
+      b.hop(st * (I == 0), st * (I == 1), st * (I == 2), 0, DD_PLAIN);
+      for (int q = 0; q < 2; ++q) {
+        int qo, u;
+        sigma_of(I, q, qo, u);
+        const int up = dir == 0 ? u : neg_unit(u);  // sign of b on h+
+        b.act(V, dir == 1, dir == 1, HP(q), AP(q), SA, U_P1, AP(qo), SB, up);
+        b.act(V, dir == 1, dir == 1, HM(q), AM(q), SA, U_P1, AM(qo), SB, neg_unit(up));
+      }
+    }
+  }
+  // diagonal pairs (I, J): V at x +- (I + J) with +-(s_I + s_J), X at x +- (I - J) with +-(s_I - s_J)
+  const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+  for (int P = 0; P < 3; ++P) {
+    const int I = pairs[P][0], J = pairs[P][1];
+    for (int form = 0; form < 2; ++form) {      // 0: V (I + J), 1: X (I - J)
+      const int sj = form == 0 ? 1 : -1;         // sign of J in the offset and of s_J
+      const int m = form == 0 ? M_VIJ + P : M_XIJ + P;
+      for (int dir = 0; dir < 2; ++dir) {        // 0: forward (matrix at x), 1: backward (at the neighbour)
+        const int st = dir == 0 ? 1 : -1;
+        b.hop(st * ((I == 0) + sj * (J == 0)), st * ((I == 1) + sj * (J == 1)), st * ((I == 2) + sj * (J == 2)), 0,
+              DD_PLAIN);
+        for (int q = 0; q < 2; ++q) {
+          int qi, ui, qj, uj;
+          sigma_of(I, q, qi, ui);
+          sigma_of(J, q, qj, uj);
+          // on h+: forward +s_I + sj s_J, backward the negative; on h-: the negative of h+
+          int pi = ui, pj = sj > 0 ? uj : neg_unit(uj);
+          if (dir == 1) { pi = neg_unit(pi); pj = neg_unit(pj); }
+          b.act(m, dir == 1, dir == 1, HP(q), AP(qi), S1, pi, AP(qj), S1, pj);
+          b.act(m, dir == 1, dir == 1, HM(q), AM(qi), S1, neg_unit(pi), AM(qj), S1, neg_unit(pj));
+        }
+      }
+    }
+  }
+  if (b.nh != DD_HOPS || b.na != DD_ACTS) b.t.hop[0].count = 0;  // malformed: launch_apply_dd refuses it
+  return b.t;
+}
+
+// ---------------------------------------------------------------------------- double-float pieces
+__device__ __forceinline__ cx<dd> ld4(const float4* p) {
+  const float4 v = __ldg(p);
+  return mk(dd(v.x, v.y), dd(v.z, v.w));
+}
+// (s, t) = a * b as an unnormalised pair: s the rounded product of the high parts, t the rest.
+__device__ __forceinline__ void prod_first(float& s, float& t, dd a, dd b) {
+  s = a.hi * b.hi;
+  t = fmaf(a.hi, b.hi, -s);
+  t = fmaf(a.hi, b.lo, t);
+  t = fmaf(a.lo, b.hi, t);
+}
+// (s, t) += a * b: TwoSum of the high parts, every low-order term into t.
+__device__ __forceinline__ void prod_acc(float& s, float& t, dd a, dd b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float s2 = s + p;
+  const float bb = s2 - s;
+  t += (s - (s2 - bb)) + (p - bb);
+  t += e;
+  s = s2;
+}
+__device__ __forceinline__ dd dneg(dd a) { return dd(-a.hi, -a.lo); }
+
+// y = V v (ADJ: V^dag v) for the matrix at wp (element e at wp + e * LANES).
+template <bool ADJ>
+__device__ __forceinline__ void matvec(const float4* __restrict__ wp, const cx<dd> (&v)[3], cx<dd> (&y)[3]) {
+  cx<dd> e[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) e[k] = ld4(wp + k * LANES);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    float sr, tr, si, ti_;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cx<dd> a = ADJ ? e[3 * c + r] : e[3 * r + c];
+      // plain: (a.re v.re - a.im v.im) + i (a.re v.im + a.im v.re)
+      // adjoint (conj a): (a.re v.re + a.im v.im) + i (a.re v.im - a.im v.re)
+      const dd aim_re = ADJ ? a.im : dneg(a.im);
+      const dd aim_im = ADJ ? dneg(a.im) : a.im;
+      if (c == 0) {
+        prod_first(sr, tr, a.re, v[c].re);
+        prod_first(si, ti_, a.re, v[c].im);
+      } else {
+        prod_acc(sr, tr, a.re, v[c].re);
+        prod_acc(si, ti_, a.re, v[c].im);
+      }
+      prod_acc(sr, tr, aim_re, v[c].im);
+      prod_acc(si, ti_, aim_im, v[c].re);
+    }
+    y[r] = mk(dd_renorm(sr, tr), dd_renorm(si, ti_));
+  }
+}
+
+__device__ __forceinline__ cx<dd> times_unit(cx<dd> y, int u) {
+  switch (u) {
+    case U_P1: return y;
+    case U_PI: return mk(dneg(y.im), y.re);
+    case U_M1: return mk(dneg(y.re), dneg(y.im));
+    case U_MI: return mk(y.im, dneg(y.re));
+    case U_1PI: return mk(y.re - y.im, y.re + y.im);
+    case U_1MI: return mk(y.re + y.im, y.im - y.re);
+    case U_M1MI: return mk(y.im - y.re, dneg(y.re + y.im));
+    default: return mk(dneg(y.re + y.im), y.re - y.im);  // -1 + i
+  }
+}
+
+// Neighbour x + d of the site with coordinates c, with the fermion sign of every wrap across an
+// antiperiodic boundary (|d_mu| <= 2, so at most two wraps per direction).
+__device__ __forceinline__ int nbr_of(const int (&c)[4], const Geom& g, const DDHop& hop, bool& neg) {
+  int n = 0;
+  neg = false;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int L = g.L[mu];
+    int x = c[mu] + hop.d[mu];
+    int wraps = 0;
+    if (x >= L) { x -= L; wraps = 1; if (x >= L) { x -= L; wraps = 2; } }
+    if (x < 0) { x += L; wraps = 1; if (x < 0) { x += L; wraps = 2; } }
+    if (((g.bcneg >> mu) & 1) && (wraps & 1)) neg = !neg;
+    n += x * g.S[mu];
+  }
+  return n;
+}
+
+// Prefetch into L1 (no registers held): the next entry's matrix, the next offset's spinor.
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+__device__ __forceinline__ const float4* wmat_dd(const float4* W, int site, int m) {
+  return W + ((size_t)(site >> 5) * NMAT + m) * (9 * LANES) + (site & 31);
+}
+__device__ __forceinline__ void prefetch_mat(const float4* wp) {
+#pragma unroll
+  for (int e = 0; e < 9; ++e) prefetch_l1(wp + e * LANES);
+}
+
+__device__ __forceinline__ void accumulate(cx<dd> (&acc)[3], const cx<dd> (&w)[3], int sc, dd f) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (sc == S1) {
+      acc[k].re = acc[k].re + w[k].re;
+      acc[k].im = acc[k].im + w[k].im;
+    } else {
+      acc[k].re = fma(f, w[k].re, acc[k].re);
+      acc[k].im = fma(f, w[k].im, acc[k].im);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------- the kernel
+template <int EPI>
+__global__ void __launch_bounds__(DD_THREADS, OK_DD_MINB)
+    apply_dd_kernel(const float4* __restrict__ W, const float4* __restrict__ psi, double2* __restrict__ out, Geom g,
+                    dd c0q2, dd a_ii, dd b_ii, const double2* __restrict__ rhs, RedArgs ra, unsigned* ticket,
+                    const int* halt, const __grid_constant__ DDTable tab) {
+  if (EPI != EPI_NONE && halt && *halt) return;
+  // Three half-spinor slots per thread, [slot * 6 + spin * 3 + colour][thread]: a thread's
+  // accesses to one entry hit consecutive 16-byte words across the warp.
+  __shared__ float4 slot[18][DD_THREADS];
+  const int tid = threadIdx.x;
+  const int s = blockIdx.x * DD_THREADS + tid;
+  double red[2] = {0.0, 0.0};
+  if (s < g.V) {
+    int c[4];
+    {
+      int r = s;
+      c[0] = r % g.L[0]; r /= g.L[0];
+      c[1] = r % g.L[1]; r /= g.L[1];
+      c[2] = r % g.L[2]; c[3] = r / g.L[2];
+    }
+    cx<dd> acc0[3], acc1[3], acc2[3], acc3[3];
+    bool neg_next;
+    int n_next = nbr_of(c, g, tab.hop[0], neg_next);
+#pragma unroll 1
+    for (int hh = 0; hh < DD_HOPS; ++hh) {
+      const DDHop hop = tab.hop[hh];
+      const int n = n_next;
+      const bool neg = neg_next;
+      // the next offset's neighbour: its spinor is prefetched now, its first matrix with this
+      // offset's last entry
+      if (hh + 1 < DD_HOPS) {
+        n_next = nbr_of(c, g, tab.hop[hh + 1], neg_next);
+        const float4* pn = psi + (size_t)n_next * 12;
+        prefetch_l1(pn);
+        prefetch_l1(pn + 8);
+        prefetch_l1(pn + 11);
+      }
+      {
+        const float4* pp = psi + (size_t)n * 12;
+        cx<dd> v[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          v[k] = ld4(pp + k);
+          if (neg) v[k] = mk(dneg(v[k].re), dneg(v[k].im));
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const cx<dd> u = v[3 * q + k], l = v[3 * (q + 2) + k];
+            cx<dd> h0, h1;
+            if (hop.kind == DD_ONSITE) {
+              h0 = mk(u.re + l.im, u.im - l.re);  // u - i l
+              h1 = mk(u.re - l.im, u.im + l.re);  // u + i l
+            } else {
+              h0 = mk(u.re + l.re, u.im + l.im);
+              h1 = mk(u.re - l.re, u.im - l.im);
+            }
+            slot[0 * 6 + 3 * q + k][tid] = make_float4(h0.re.hi, h0.re.lo, h0.im.hi, h0.im.lo);
+            slot[1 * 6 + 3 * q + k][tid] = make_float4(h1.re.hi, h1.re.lo, h1.im.hi, h1.im.lo);
+            if (hop.kind == DD_THIRD_L || hop.kind == DD_THIRD_U) {
+              const cx<dd> t3 = hop.kind == DD_THIRD_L ? l : u;
+              slot[2 * 6 + 3 * q + k][tid] = make_float4(t3.re.hi, t3.re.lo, t3.im.hi, t3.im.lo);
+            }
+          }
+        if (hop.kind == DD_ONSITE) {
+          // the c0q part of W^0: acc+ = 2 c0q (u + l), acc- = 2 c0q (u - l)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const cx<dd> u0 = v[k], u1 = v[3 + k], l0 = v[6 + k], l1 = v[9 + k];
+            acc0[k] = mk(c0q2 * (u0.re + l0.re), c0q2 * (u0.im + l0.im));
+            acc1[k] = mk(c0q2 * (u1.re + l1.re), c0q2 * (u1.im + l1.im));
+            acc2[k] = mk(c0q2 * (u0.re - l0.re), c0q2 * (u0.im - l0.im));
+            acc3[k] = mk(c0q2 * (u1.re - l1.re), c0q2 * (u1.im - l1.im));
+          }
+        }
+      }
+      const int a_end = hop.first + hop.count;
+#pragma unroll 1
+      for (int ai = hop.first; ai < a_end; ++ai) {
+        const DDAct A = tab.act[ai];
+        const int ws = (A.flags & 1) ? n : s;
+        const int src = A.flags >> 2;
+        const float4* wp = wmat_dd(W, ws, A.m);
+        if (ai + 1 < a_end) {
+          const DDAct B = tab.act[ai + 1];
+          prefetch_mat(wmat_dd(W, (B.flags & 1) ? n : s, B.m));
+        } else if (hh + 1 < DD_HOPS) {
+          const DDAct B = tab.act[tab.hop[hh + 1].first];
+          prefetch_mat(wmat_dd(W, (B.flags & 1) ? n_next : s, B.m));
+        }
+        cx<dd> v[3], y[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float4 f = slot[src * 3 + k][tid];
+          v[k] = mk(dd(f.x, f.y), dd(f.z, f.w));
+        }
+        if (A.flags & 2) matvec<true>(wp, v, y);
+        else matvec<false>(wp, v, y);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int d = A.dst[j];
+          if (d < 0) continue;
+          const int sc = A.mul[j] & 3, un = A.mul[j] >> 2;
+          cx<dd> w[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) w[k] = times_unit(y[k], un);
+          const dd f = sc == SA ? a_ii : b_ii;
+          switch (d) {
+            case 0: accumulate(acc0, w, sc, f); break;
+            case 1: accumulate(acc1, w, sc, f); break;
+            case 2: accumulate(acc2, w, sc, f); break;
+            default: accumulate(acc3, w, sc, f); break;
+          }
+        }
+      }
+    }
+    // out_u = acc+ + acc-, out_l = acc+ - acc-, rounded to FP64
+    double2* op = out + (size_t)s * 12;
+    const double2* bp = EPI == EPI_RESID ? rhs + (size_t)s * 12 : nullptr;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const cx<dd> p = q == 0 ? acc0[k] : acc1[k];
+        const cx<dd> m = q == 0 ? acc2[k] : acc3[k];
+        const cx<dd> up = mk(p.re + m.re, p.im + m.im), lo = mk(p.re - m.re, p.im - m.im);
+        double2 ou = make_double2((double)up.re, (double)up.im);
+        double2 ol = make_double2((double)lo.re, (double)lo.im);
+        if (EPI == EPI_RESID) {
+          const double2 bu = bp[3 * q + k], bl = bp[3 * (q + 2) + k];
+          ou = make_double2(bu.x - ou.x, bu.y - ou.y);
+          ol = make_double2(bl.x - ol.x, bl.y - ol.y);
+          red[0] += ou.x * ou.x + ou.y * ou.y + ol.x * ol.x + ol.y * ol.y;
+          red[1] += bu.x * bu.x + bu.y * bu.y + bl.x * bl.x + bl.y * bl.y;
+        }
+        op[3 * q + k] = ou;
+        op[3 * (q + 2) + k] = ol;
+      }
+  }
+  if (EPI == EPI_RESID) grid_reduce<2, DD_THREADS>(red, ra, ticket);
+}
+
+}  // namespace
+
+const DDTable& dd_table() {
+  static const DDTable t = build_table();
+  return t;
+}
+
+int launch_apply_dd(const ok_W* Wh, const cx<dd>* psi_df, cx<double>* out, int epi, const EpiArgs<dd>& ep, cudaStream_t st) {
+  if (!Wh->Wdf || (epi != EPI_NONE && epi != EPI_RESID)) return OK_EINVAL;
+  if (epi == EPI_RESID && !ep.b) return OK_EINVAL;
+  const DDTable& tab = dd_table();
+  if (tab.hop[0].count == 0) return OK_EINTERNAL;
+  const Geom& g = Wh->g;
+  const int nb = grid_for(g.V, DD_THREADS);
+  const dd c0q2(2.0 * Wh->sc.c0q), a(Wh->sc.a_ii), b(Wh->sc.b_ii);
+  const float4* W = reinterpret_cast<const float4*>(Wh->Wdf);
+  const float4* psi = reinterpret_cast<const float4*>(psi_df);
+  double2* o = reinterpret_cast<double2*>(out);
+  const double2* rhs = reinterpret_cast<const double2*>(ep.b);
+  {
+    TraceScope ts(epi == EPI_RESID ? "apply_df64_resid" : "apply_df64", st);
+    if (epi == EPI_RESID)
+      apply_dd_kernel<EPI_RESID><<<nb, DD_THREADS, 0, st>>>(W, psi, o, g, c0q2, a, b, rhs, ep.ra, ep.ticket, ep.halt, tab);
+    else
+      apply_dd_kernel<EPI_NONE><<<nb, DD_THREADS, 0, st>>>(W, psi, o, g, c0q2, a, b, rhs, ep.ra, ep.ticket, ep.halt, tab);
+  }
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+}  // namespace okgb

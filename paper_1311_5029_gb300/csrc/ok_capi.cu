@@ -1,4 +1,5 @@
 // The extern "C" boundary declared in include/ok.h: argument checks, error codes, launch count.
+#include "ok_dd.cuh"
 #include "ok_launch.cuh"
 
 #include <atomic>
@@ -131,7 +132,7 @@ int ok_apply_M(const ok_W* W, ok_prec prec, const void* psi, void* out, void* st
     int rc = launch_to_df((const cx<double>*)psi, (cx<dd>*)psi_df, 12LL * W->g.V, st);
     if (rc == OK_SUCCESS) {
       EpiArgs<dd> e{};
-      rc = launch_apply_df(W, (const cx<dd>*)psi_df, (cx<double>*)out, EPI_NONE, e, st);
+      rc = launch_apply_dd(W, (const cx<dd>*)psi_df, (cx<double>*)out, EPI_NONE, e, st);
     }
     cudaError_t fe = cudaFreeAsync(psi_df, st);
     if (rc == OK_SUCCESS && fe != cudaSuccess) { set_cuda_error(fe); rc = OK_ECUDA; }

@@ -24,8 +24,6 @@ template <typename R> struct EpiArgs {
 template <typename R>
 int launch_apply(const ok_W* W, const cx<R>* psi, cx<R>* out, int epi, const EpiArgs<R>& ep, cudaStream_t st);
 int apply_blocks_needed(const ok_W* W);
-// FP64-accurate apply with the double-float W copy (psi double-float, out FP64; EPI_NONE/EPI_RESID).
-int launch_apply_df(const ok_W* W, const cx<dd>* psi_df, cx<double>* out, int epi, const EpiArgs<dd>& ep, cudaStream_t st);
 // FP32 fields and arithmetic with the half-precision W copy (all epilogues).
 int launch_apply_w16(const ok_W* W, const cx<float>* psi, cx<float>* out, int epi, const EpiArgs<float>& ep, cudaStream_t st);
 // Bounded device waits that gave up (the kernel's result is then invalid); optionally reset.

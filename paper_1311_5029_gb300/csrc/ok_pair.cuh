@@ -33,14 +33,7 @@ template <typename R>
 __device__ __forceinline__ M3<R> wmat(const cx<R>* __restrict__ W, int site, int m) {
   const size_t base = ((size_t)(site >> 5) * NMAT + m) * (9 * LANES) + (site & 31);
   M3<R> a;
-  if constexpr (std::is_same<R, dd>::value) {
-    const float4* p = reinterpret_cast<const float4*>(W) + base;
-#pragma unroll
-    for (int e = 0; e < 9; ++e) {
-      float4 d = __ldg(p + e * LANES);
-      a.e[e] = mk<R>(dd(d.x, d.y), dd(d.z, d.w));
-    }
-  } else if constexpr (std::is_same<R, double>::value) {
+  if constexpr (std::is_same<R, double>::value) {
     const double2* p = reinterpret_cast<const double2*>(W) + base;
 #pragma unroll
     for (int e = 0; e < 9; ++e) {

@@ -19,6 +19,7 @@
 // r = b - M x with the FP64 W (the true residual) and continues from it with the same search
 // direction (Sleijpen and van der Vorst, "Reliable updated residuals in hybrid Bi-CG methods",
 // Computing 56 (1996) 141).  The iteration stops when the FP64 true residual is below tol.
+#include "ok_dd.cuh"
 #include "ok_launch.cuh"
 #include "ok_net.cuh"
 
@@ -139,19 +140,20 @@ int iterate(const ok_W* W, const IterBufs<R>& b, long long n, SolverState* dst, 
 }
 
 // out = b - M x in FP64 with |out|^2 in state aux[0] and |b|^2 in state bb (and aux[1]).  With the
-// native FP64 W copy when the handle has one, else with the double-float copy (x converted first
-// into `xdf`, n complex double-floats of scratch).
+// double-float copy when the handle has one (x converted first into `xdf`, n complex double-floats
+// of scratch): on the FP32 pipes it is faster than the native FP64 copy, which is used otherwise.
 int residual64(const ok_W* W, const cx<double>* bvec, const cx<double>* x, cx<double>* out, SolverState* dst, double* part,
                cx<dd>* xdf, cudaStream_t st) {
-  if (W->W64) {
-    EpiArgs<double> e{nullptr, bvec, RedArgs{dst, part, nullptr, FIN_RESID}, &dst->ticket[5], nullptr};
-    return launch_apply<double>(W, x, out, EPI_RESID, e, st);
+  if (W->Wdf) {
+    if (!xdf) return OK_EINVAL;
+    OK_TRY(launch_to_df(x, xdf, 12LL * W->g.V, st));
+    EpiArgs<dd> e{nullptr, reinterpret_cast<const cx<dd>*>(bvec), RedArgs{dst, part, nullptr, FIN_RESID}, &dst->ticket[5],
+                  nullptr};
+    return launch_apply_dd(W, xdf, out, EPI_RESID, e, st);
   }
-  if (!W->Wdf || !xdf) return OK_EINVAL;
-  OK_TRY(launch_to_df(x, xdf, 12LL * W->g.V, st));
-  EpiArgs<dd> e{nullptr, reinterpret_cast<const cx<dd>*>(bvec), RedArgs{dst, part, nullptr, FIN_RESID}, &dst->ticket[5],
-                nullptr};
-  return launch_apply_df(W, xdf, out, EPI_RESID, e, st);
+  if (!W->W64) return OK_EINVAL;
+  EpiArgs<double> e{nullptr, bvec, RedArgs{dst, part, nullptr, FIN_RESID}, &dst->ticket[5], nullptr};
+  return launch_apply<double>(W, x, out, EPI_RESID, e, st);
 }
 
 }  // namespace
@@ -205,7 +207,7 @@ int bicgstab_impl(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok
   cx<double>* r64 = ws.get<cx<double>>(n, &err);
   if (!r64) { set_cuda_error(err); return OK_ENOMEM; }
   cx<dd>* xdf = nullptr;
-  if (!W->W64) {
+  if (W->Wdf) {
     xdf = ws.get<cx<dd>>(n, &err);
     if (!xdf) { set_cuda_error(err); return OK_ENOMEM; }
   }
@@ -338,9 +340,9 @@ int true_residual(const ok_W* W, const cx<double>* bvec, const cx<double>* x, do
   double* part = ws.get<double>((size_t)apply_blocks_needed(W) * 4, &err);
   SolverState* dst = ws.get<SolverState>(1, &err);
   cx<double>* r = ws.get<cx<double>>(n, &err);
-  cx<dd>* xdf = W->W64 ? nullptr : ws.get<cx<dd>>(n, &err);
+  cx<dd>* xdf = W->Wdf ? ws.get<cx<dd>>(n, &err) : nullptr;
   HostState hs;
-  if (!part || !dst || !r || !hs.h || (!W->W64 && !xdf)) { if (err != cudaSuccess) set_cuda_error(err); return OK_ENOMEM; }
+  if (!part || !dst || !r || !hs.h || (W->Wdf && !xdf)) { if (err != cudaSuccess) set_cuda_error(err); return OK_ENOMEM; }
   OK_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(SolverState), st));
   OK_TRY(residual64(W, bvec, x, r, dst, part, xdf, st));
   OK_TRY(read_state(dst, hs.h, st));
@@ -415,7 +417,7 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
   double* part = ws.get<double>((size_t)pstride * nrhs, &err);
   SolverState* dst = ws.get<SolverState>(nrhs, &err);
   cx<double>* r64 = ws.get<cx<double>>(n, &err);
-  cx<dd>* xdf = W->W64 ? nullptr : ws.get<cx<dd>>(n, &err);
+  cx<dd>* xdf = W->Wdf ? ws.get<cx<dd>>(n, &err) : nullptr;
   IterBufs<float> b{};
   b.x = ws.get<cx<float>>(N, &err); b.r = ws.get<cx<float>>(N, &err); b.rhat = ws.get<cx<float>>(N, &err);
   b.p = ws.get<cx<float>>(N, &err); b.v = ws.get<cx<float>>(N, &err); b.s = ws.get<cx<float>>(N, &err);
@@ -428,7 +430,7 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
   SolverState* h = nullptr;
   if (cudaMallocHost((void**)&h, sizeof(SolverState) * nrhs) != cudaSuccess) h = nullptr;
   struct HostFree { SolverState* p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{h};
-  if (!part || !dst || !r64 || (!W->W64 && !xdf) || !b.x || !b.r || !b.rhat || !b.p || !b.v || !b.s || !b.t || !h) {
+  if (!part || !dst || !r64 || (W->Wdf && !xdf) || !b.x || !b.r || !b.rhat || !b.p || !b.v || !b.s || !b.t || !h) {
     if (err != cudaSuccess) set_cuda_error(err);
     return OK_ENOMEM;
   }

@@ -11,10 +11,13 @@ import bench
 
 def test_byte_model():
     assert bench.APPLY32 == 3288 and bench.APPLY64 == 6576
-    assert bench.W32_BYTES == 43 * 9 * 8
+    assert bench.W32_BYTES == 43 * 9 * 8 and bench.WDF_BYTES == 2 * bench.W64_BYTES
+    # double-float residual: x converted (192 in, 384 out), W_df + x_df + b read, r written
+    assert bench.RESIDDF == 192 + 384 + 12384 + 384 + 2 * 192
+    assert bench.PRECOMPUTE["mixed"] == 576 + 12384 + 3096 and bench.PRECOMPUTE["f64"] == 576 + 6192
     info = dict(iters=10, fp64_applies=2, reliable_updates=1, restarts=0)
     V = 1000
-    expect = V * (10 * (2 * 3288 + bench.ITER_VEC32) + 2 * bench.RESID64 + 2 * bench.RELIABLE32)
+    expect = V * (10 * (2 * 3288 + bench.ITER_VEC32) + 2 * bench.RESIDDF + 2 * bench.RELIABLE32)
     assert bench.solve_bytes(V, info, "mixed") == expect
     assert bench.solve_bytes(V, dict(iters=0, fp64_applies=0, reliable_updates=0, restarts=0), "f64") == \
         V * bench.RESTART64

@@ -206,6 +206,29 @@ def test_double_float_true_residual_equals_native():
     assert abs(rn - rd) < 1e-12 * rn
 
 
+def test_handle_with_both_fp64_copies():
+    """With OK_W_F64 and OK_W_DF64 on one handle, ok_apply_M in FP64 runs the native kernel and
+    the true residual the double-float one (the launch classes recorded by the trace); both meet
+    the FP64 bar against the oracle."""
+    dims, bc = (5, 4, 6, 4), (1, 1, 1, -1)
+    U = synth.random_links(dims, 0.3, 5401)
+    c = synth.random_coeffs(5402)
+    W = ok.precompute_W(to_dev(U), c, bc, ok.W_F64 | ok.W_DF64)
+    b = synth.gaussian_source(dims, 5403)
+    x = 0.3 * synth.gaussian_source(dims, 5404)
+    ok.trace_reset()
+    ok.trace_enable(True)
+    got = ok.apply_M(W, to_dev(x)).cpu().numpy()
+    rel = ok.true_residual(W, to_dev(b), to_dev(x))
+    ok.trace_enable(False)
+    tr = ok.trace_read()
+    assert tr.get("apply_f64", (0, 0))[0] == 1 and tr.get("apply_df64_resid", (0, 0))[0] == 1, tr
+    Mx = wform.apply(U, c, x, bc)
+    assert rel_l2(got, Mx) < FP64_TOL
+    exp = np.linalg.norm(b - Mx) / np.linalg.norm(b)
+    assert abs(rel - exp) < FP64_TOL * exp
+
+
 def test_double_float_16cube32_sampled():
     dims, U, c, src = synth.workload_inputs("16^3x32")
     W = ok.precompute_W(to_dev(U), c, (1, 1, 1, 1), ok.W_DF64 | ok.W_F32)
