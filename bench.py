@@ -298,13 +298,18 @@ def run_ours(args):
     per_launch = APPLY32 if args.mode == "mixed" else APPLY64
     n_apply = sum(v[0] for k, v in trace.items() if k in (key + "_dot", key + "_ts"))
     ms_apply = sum(v[1] for k, v in trace.items() if k in (key + "_dot", key + "_ts"))
+    # Every executed iteration applies M twice (v = M p and t = M s); the remaining launches of the
+    # class belong to iterations enqueued after the state halted, which return at once.  All the
+    # class's time is charged to the launches that do the work.
+    n_work = 2 * sum(i["iters"] for i in infos)
     peak, peak_kind = measured_peaks()
-    achieved = per_launch * V / (ms_apply / n_apply * 1e-3) / 1e9 if n_apply else None
+    avg_us = ms_apply / n_work * 1e3 if n_work else None
+    achieved = per_launch * V / (avg_us * 1e-6) / 1e9 if n_work else None
     traffic = ncu_traffic(key)
     roof = {"kernel": key, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_source": peak_kind,
             "unit": "GB/s", "frac": achieved / peak if achieved else None, "traffic": traffic,
-            "algorithmic_bytes_per_launch": per_launch * V, "launches": n_apply,
-            "avg_launch_us": ms_apply / n_apply * 1e3 if n_apply else None}
+            "algorithmic_bytes_per_launch": per_launch * V, "launches": n_work,
+            "launches_after_halt": n_apply - n_work, "avg_launch_us": avg_us}
     step_ms = sum(v[1] for v in trace.values())
     shares = {k: round(v[1] / step_ms, 4) for k, v in sorted(trace.items(), key=lambda kv: -kv[1][1])} if step_ms else {}
 
