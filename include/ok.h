@@ -253,7 +253,7 @@ int ok_true_residual(const ok_W* W, const void* b, const void* x, double* relres
  *     a cudaMalloc issued here would fail or fragment that pool;
  *   - latency-critical loops that cannot afford the device-wide synchronisation cudaMalloc and
  *     cudaFree imply.
- * It computes r = b - M x with the FP64 W (one fused application of M) and *relres = |r| / |b|
+ * It computes r = b - M x with the OK_W_F64 copy (one fused application of M) and *relres = |r| / |b|
  * (|M x| when b = 0), like ok_true_residual, but calls no cudaMalloc, cudaFree or allocating
  * routine.
  *   b, x: device [V][4][3] complex128, inputs.  r: device [V][4][3] complex128, output, supplied by

@@ -486,7 +486,7 @@ def bicgstab_net(W: WHandle, net: Net, src, x=None, tol=1e-10, maxiter=20000, mo
 
 
 def true_residual(W: WHandle, b, x, stream=None) -> float:
-    """ok_true_residual: |b - M x| / |b| with the FP64 W."""
+    """ok_true_residual: |b - M x| / |b| with an FP64-accurate W (double-float copy if present, else FP64)."""
     import torch
     for t, n in ((b, "b"), (x, "x")):
         _field_check(W, t, n)

@@ -964,8 +964,6 @@ int read_wait_timeouts(unsigned* n, bool reset) {
   return OK_SUCCESS;
 }
 
-// FP64-accurate application with the double-float copy of W: psi in double-float, out in FP64;
-// EPI_NONE or EPI_RESID (b in FP64).  One thread per site, as for native FP64.
 template int launch_apply<double>(const ok_W*, const cx<double>*, cx<double>*, int, const EpiArgs<double>&, cudaStream_t);
 template int launch_apply<float>(const ok_W*, const cx<float>*, cx<float>*, int, const EpiArgs<float>&, cudaStream_t);
 

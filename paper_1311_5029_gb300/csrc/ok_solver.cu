@@ -16,7 +16,8 @@
 // Mixed mode: the iteration runs in FP32 on the FP32 copy of W with its own solution increment
 // x32; x and the true residual stay FP64.  When the FP32 residual has dropped by delta against its
 // maximum since the last update (or reaches tol), a reliable update folds x32 into x, recomputes
-// r = b - M x with the FP64 W (the true residual) and continues from it with the same search
+// r = b - M x with an FP64-accurate W (the true residual: the double-float copy when the handle has
+// one, else the native FP64 copy) and continues from it with the same search
 // direction (Sleijpen and van der Vorst, "Reliable updated residuals in hybrid Bi-CG methods",
 // Computing 56 (1996) 141).  The iteration stops when the FP64 true residual is below tol.
 #include "ok_dd.cuh"
