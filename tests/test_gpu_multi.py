@@ -100,12 +100,15 @@ def test_multi_argument_errors():
         ok.bicgstab_multi(W, b, mode=ok.SOLVE_F64)
 
 
+@pytest.mark.parametrize("w64", ["f64", "df64"])
 @pytest.mark.parametrize("mode", ["mixed", "mixed16"])
-def test_multi_solve_spin_colour_sources_small(mode):
+def test_multi_solve_spin_colour_sources_small(mode, w64):
+    """Every system to its own true residual, with the residuals on the native FP64 copy or on
+    the double-float one."""
     dims, bc = (6, 5, 4, 8), (1, 1, 1, -1)
     U = synth.random_links(dims, 0.3, 8501)
     c = synth.placeholder_coeffs(0.6)
-    W = ok.precompute_W(to_dev(U), c, bc, ok.W_F64 | ok.W_F32 | ok.W_F16)
+    W = ok.precompute_W(to_dev(U), c, bc, (ok.W_F64 if w64 == "f64" else ok.W_DF64) | ok.W_F32 | ok.W_F16)
     b = spin_colour_sources(dims, site=17)
     m = ok.SOLVE_MIXED if mode == "mixed" else ok.SOLVE_MIXED16
     x, infos = ok.bicgstab_multi(W, b, tol=1e-10, mode=m, delta=1e-2, check_every=4)
@@ -117,7 +120,7 @@ def test_multi_solve_spin_colour_sources_small(mode):
         assert abs(infos[k]["true_relres"] - r) < 1e-12
     # the same systems solved one at a time agree
     for k in (0, 7):
-        xk, ik = ok.bicgstab(W, b[k].contiguous(), tol=1e-10, mode=ok.SOLVE_F64)
+        xk, ik = ok.bicgstab(W, b[k].contiguous(), tol=1e-10, mode=ok.SOLVE_F64 if w64 == "f64" else ok.SOLVE_MIXED)
         assert rel_l2(xs[k], xk.cpu().numpy()) < 1e-8
 
 
