@@ -62,3 +62,16 @@ def test_two_rank_max_time_sum_units():
         p.join(timeout=30)
         assert p.exitcode == 0
     assert out == [(0, 11.0, 300.0), (1, 11.0, 300.0)]
+
+
+def test_reference_arm_line(capsys):
+    """`bench.py --impl reference` times the oracle on the host and prints the contract's JSON line
+    (one step on the full workload, about ten seconds of CPU)."""
+    import json
+    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "GB/s"
+    assert line["higher_is_better"] is True and line["steps"] == 1 and line["n_gpus"] == 1
+    assert line["config"]["workload"] == bench.WORKLOAD and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
