@@ -284,12 +284,13 @@ __global__ void __launch_bounds__(DD_THREADS, OK_DD_MINB)
   if (EPI == EPI_RESID) grid_reduce<2, DD_THREADS>(red, ra, ticket);
 }
 
-}  // namespace
-
+// The table, built once on the host.
 const DDTable& dd_table() {
   static const DDTable t = build_table();
   return t;
 }
+
+}  // namespace
 
 int launch_apply_dd(const ok_W* Wh, const cx<dd>* psi_df, cx<double>* out, int epi, const EpiArgs<dd>& ep, cudaStream_t st) {
   if (!Wh->Wdf || (epi != EPI_NONE && epi != EPI_RESID)) return OK_EINVAL;

@@ -10,7 +10,7 @@ namespace okgb {
 int launch_apply_dd(const ok_W* W, const cx<dd>* psi_df, cx<double>* out, int epi, const EpiArgs<dd>& ep, cudaStream_t st);
 
 // The stencil as the table the kernel walks: 27 offsets, each with its colour matrix-vector
-// products.  Exposed for the host-side consistency check of the table (counts and ranges).
+// products (built by ok_dd_table.cuh, passed to the kernel as a launch parameter).
 struct DDHop {
   signed char d[4];       // offset (x, y, z, t)
   unsigned char kind;     // DD_ONSITE, DD_PLAIN, DD_THIRD_L, DD_THIRD_U
@@ -33,7 +33,5 @@ struct DDTable {
   DDHop hop[DD_HOPS];
   DDAct act[DD_ACTS];
 };
-// The table (built once on the host).
-const DDTable& dd_table();
 
 }  // namespace okgb
