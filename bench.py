@@ -209,6 +209,23 @@ def ncu_traffic(kernel_key):
     return float(m_b.group(1))
 
 
+def roofline(trace, infos, key, bytes_per_launch, peak, peak_kind, traffic):
+    """The roofline record of the apply class `key` from the trace ({class: (launches, ms)}) and the
+    solves' info records.  Every executed iteration applies M twice (v = M p and t = M s); the other
+    launches of the class belong to iterations enqueued after the state halted, which return at once,
+    so the class's whole time is charged to the 2 x iterations launches that do the work."""
+    names = (key + "_dot", key + "_ts")
+    n_apply = sum(v[0] for k, v in trace.items() if k in names)
+    ms_apply = sum(v[1] for k, v in trace.items() if k in names)
+    n_work = 2 * sum(i["iters"] for i in infos)
+    avg_us = ms_apply / n_work * 1e3 if n_work else None
+    achieved = bytes_per_launch / (avg_us * 1e-6) / 1e9 if n_work else None
+    return {"kernel": key, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_source": peak_kind,
+            "unit": "GB/s", "frac": achieved / peak if achieved else None, "traffic": traffic,
+            "algorithmic_bytes_per_launch": bytes_per_launch, "launches": n_work,
+            "launches_after_halt": n_apply - n_work, "avg_launch_us": avg_us}
+
+
 # ----------------------------------------------------------------------------- oracle timing
 def oracle_sample(dims, U, c, b):
     """One oracle application of M on the full lattice: (seconds, threads used, bytes counted)."""
@@ -296,20 +313,8 @@ def run_ours(args):
     # dominant kernel: the FP32 (or FP64) application of M inside the solve
     key = "apply_f32" if args.mode == "mixed" else "apply_f64"
     per_launch = APPLY32 if args.mode == "mixed" else APPLY64
-    n_apply = sum(v[0] for k, v in trace.items() if k in (key + "_dot", key + "_ts"))
-    ms_apply = sum(v[1] for k, v in trace.items() if k in (key + "_dot", key + "_ts"))
-    # Every executed iteration applies M twice (v = M p and t = M s); the remaining launches of the
-    # class belong to iterations enqueued after the state halted, which return at once.  All the
-    # class's time is charged to the launches that do the work.
-    n_work = 2 * sum(i["iters"] for i in infos)
     peak, peak_kind = measured_peaks()
-    avg_us = ms_apply / n_work * 1e3 if n_work else None
-    achieved = per_launch * V / (avg_us * 1e-6) / 1e9 if n_work else None
-    traffic = ncu_traffic(key)
-    roof = {"kernel": key, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_source": peak_kind,
-            "unit": "GB/s", "frac": achieved / peak if achieved else None, "traffic": traffic,
-            "algorithmic_bytes_per_launch": per_launch * V, "launches": n_work,
-            "launches_after_halt": n_apply - n_work, "avg_launch_us": avg_us}
+    roof = roofline(trace, infos, key, per_launch * V, peak, peak_kind, ncu_traffic(key))
     step_ms = sum(v[1] for v in trace.values())
     shares = {k: round(v[1] / step_ms, 4) for k, v in sorted(trace.items(), key=lambda kv: -kv[1][1])} if step_ms else {}
 

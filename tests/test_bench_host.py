@@ -75,3 +75,17 @@ def test_reference_arm_line(capsys):
     assert line["config"]["workload"] == bench.WORKLOAD and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_roofline_charges_time_to_working_launches():
+    """Launches of iterations enqueued after a halt return at once; the class's time is charged
+    to the 2 x iterations launches that do the work (numbers of a 16^3x32 bench line)."""
+    trace = {"apply_f32_dot": (1420, 152.0), "apply_f32_ts": (1420, 148.0), "apply_df64_resid": (60, 56.0)}
+    infos = [{"iters": 60}] * 20
+    r = bench.roofline(trace, infos, "apply_f32", bench.APPLY32 * 131072, 6790.0, "measured", None)
+    assert r["launches"] == 2400 and r["launches_after_halt"] == 440
+    assert abs(r["avg_launch_us"] - 300.0 / 2400 * 1e3) < 1e-9
+    assert abs(r["achieved"] - bench.APPLY32 * 131072 / (125e-6) / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / 6790.0) < 1e-12 and r["bound"] == "hbm"
+    empty = bench.roofline({}, [], "apply_f32", 1, 6790.0, "measured", None)
+    assert empty["achieved"] is None and empty["frac"] is None
