@@ -247,6 +247,23 @@ ok_solve_params ok_default_solve_params(double tol, int maxiter);
  * Needs OK_W_F64 or OK_W_DF64.  Synchronises `stream`.  |b| = 0 gives relres = |M x|. */
 int ok_true_residual(const ok_W* W, const void* b, const void* x, double* relres, void* stream);
 
+/* Inspection: one application of M with the fused inner products that a BiCGStab half-iteration
+ * takes from it (the paper's bi-stabilized CG, Sec. 2.3; van der Vorst 1992): the launch the
+ * solver runs for v = M p (kind OK_REDUCE_DOT) and for t = M s (kind OK_REDUCE_TS).
+ *   out = M psi, and
+ *   OK_REDUCE_DOT: sums[0] + i sums[1] = <y, M psi> = sum conj(y) (M psi); sums[2] = 0;
+ *   OK_REDUCE_TS:  sums[0] + i sums[1] = <M psi, y>, sums[2] = |M psi|^2.
+ * prec OK_F64 (complex128 fields, OK_W_F64; OK_REDUCE_TS then needs y == psi), OK_F32 (complex64,
+ * OK_W_F32) or OK_F32_W16 (complex64, OK_W_F16).  psi, y, out: device [V][4][3]; out must not
+ * overlap psi or y; sums: host, 3 doubles.  The partial sums are FP64 and summed in a fixed order.
+ * Allocates stream-ordered scratch and synchronises `stream`.
+ * Errors: OK_EINVAL (null or misaligned pointers, overlap, a missing copy, an unknown kind),
+ * OK_ENOMEM, OK_ECUDA. */
+#define OK_REDUCE_DOT 1
+#define OK_REDUCE_TS 2
+int ok_apply_M_reduce(const ok_W* W, ok_prec prec, int kind, const void* psi, const void* y, void* out,
+                      double* sums, void* stream);
+
 /* Allocation-free true residual.  The paper has no counterpart: this entry exists for callers that
  * cannot let a library allocate device memory.  Two kinds of caller need it:
  *   - programs that reserve (nearly) all of the GPU's memory for their own pool at start-up, where
@@ -259,9 +276,10 @@ int ok_true_residual(const ok_W* W, const void* b, const void* x, double* relres
  *   b, x: device [V][4][3] complex128, inputs.  r: device [V][4][3] complex128, output, supplied by
  *   the caller, must not overlap b or x.  relres: host.
  * Its reduction scratch is one fixed array of about 2 MiB in the library's device memory.  Every GPU
- * that loads the library holds that array until the process exits.  The first call on a device
- * looks up the array's address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls on a device share the array, so calls that overlap on
+ * that loads the library holds that array until the process exits.  Every call looks up the array's
+ * address (cudaGetSymbolAddress, which allocates nothing) with the caller's device current, so a
+ * device reset or a new context between calls is handled; the first call on a device may load the
+ * library's module there, so make that first call before any stream capture.  All calls on a device share the array, so calls that overlap on
  * the GPU (different streams or threads) race: serialise them.  Synchronises `stream`.
  * Errors: OK_EINVAL for null or misaligned pointers, r overlapping an input, a handle without
  * OK_W_F64, or a lattice of more than OK_STATIC_MAX_SITES sites; OK_ECUDA. */

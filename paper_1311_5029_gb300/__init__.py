@@ -23,6 +23,7 @@ __all__ = [
     "load", "precompute_W", "apply_M", "bicgstab", "true_residual", "W_expand", "launch_count",
     "strerror", "OKError", "WHandle", "F64", "F32", "F32_W16", "W_F64", "W_F32", "W_DF64", "W_F16", "W_LINKS", "Net", "net_create", "net_apply", "net_loss_grad", "net_train_step", "bicgstab_net",
     "SOLVE_AUTO", "SOLVE_F64", "SOLVE_MIXED", "SOLVE_MIXED16", "header_functions", "wait_timeouts", "apply_M_multi", "bicgstab_multi", "autotune", "set_launch_shape", "trace_enable", "trace_read", "trace_reset", "true_residual_static",
+    "apply_M_reduce", "REDUCE_DOT", "REDUCE_TS",
 ]
 
 F64, F32, F32_W16 = 0, 1, 2
@@ -89,6 +90,7 @@ def load(path: str | None = None):
         "ok_default_solve_params": (ok_solve_params, [d, i]),
         "ok_true_residual": (i, [vp, vp, vp, ctypes.POINTER(d), vp]),
         "ok_true_residual_static": (i, [vp, vp, vp, vp, ctypes.POINTER(d), vp]),
+        "ok_apply_M_reduce": (i, [vp, i, i, vp, vp, vp, ctypes.POINTER(d), vp]),
         "ok_W_expand": (i, [vp, i, i, vp, vp]),
         "ok_launch_count": (ctypes.c_ulonglong, []),
         "ok_wait_timeouts": (i, [ctypes.POINTER(ctypes.c_uint), i]),
@@ -277,6 +279,30 @@ def apply_M(W: WHandle, psi, out=None, stream=None, prec=None):
                            _stream(stream))
     _check(st, "ok_apply_M")
     return out
+
+
+REDUCE_DOT, REDUCE_TS = 1, 2
+
+
+def apply_M_reduce(W: WHandle, psi, y, kind, out=None, prec=None, stream=None):
+    """ok_apply_M_reduce: out = M psi with the fused BiCGStab inner products.  Returns (out, sums):
+    kind REDUCE_DOT: sums = (<y, M psi>, 0); REDUCE_TS: sums = (<M psi, y>, |M psi|^2)."""
+    import torch
+    _field_check(W, psi, "psi")
+    _field_check(W, y, "y")
+    if out is None:
+        out = torch.empty_like(psi)
+    _field_check(W, out, "out")
+    if not (out.dtype == psi.dtype == y.dtype):
+        raise ValueError("psi, y and out must have the same dtype")
+    if prec is None:
+        prec = F64 if psi.dtype == torch.complex128 else F32
+    sums = (ctypes.c_double * 3)()
+    st = load().ok_apply_M_reduce(W.ptr, int(prec), int(kind), ctypes.c_void_p(psi.data_ptr()),
+                                  ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(out.data_ptr()), sums,
+                                  _stream(stream))
+    _check(st, "ok_apply_M_reduce")
+    return out, (complex(sums[0], sums[1]), float(sums[2]))
 
 
 def bicgstab(W: WHandle, src, x=None, tol=1e-10, maxiter=20000, mode=SOLVE_AUTO, delta=1e-3, max_restarts=5,

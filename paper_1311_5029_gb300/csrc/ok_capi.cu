@@ -49,23 +49,36 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
-TraceScope::TraceScope(const char* n, cudaStream_t s) : name(n), st(s), slot(-1) {
+// The scope holds its own two events and hands the finished record to g_pending only in the
+// destructor, so a drain (ok_trace_read / ok_trace_reset) that runs between the two calls on another
+// thread neither loses the record nor sees one whose end event was never recorded.
+TraceScope::TraceScope(const char* n, cudaStream_t s) : name(n), st(s), a(nullptr), b(nullptr) {
   if (!g_trace_on.load(std::memory_order_relaxed)) return;
   // Kernels recorded into a CUDA graph are not timed one by one (the graph launch is).
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   std::lock_guard<std::mutex> lk(g_trace_mu);
-  TraceRec r{n, take_event(), take_event()};
-  if (!r.a || !r.b) return;
-  if (cudaEventRecord(r.a, s) != cudaSuccess) return;
-  g_pending.push_back(r);
-  slot = (int)g_pending.size() - 1;
+  cudaEvent_t ea = take_event();
+  if (!ea) return;
+  cudaEvent_t eb = take_event();
+  if (!eb || cudaEventRecord(ea, s) != cudaSuccess) {
+    g_event_pool.push_back(ea);  // nothing is timed: both events go back to the pool
+    if (eb) g_event_pool.push_back(eb);
+    return;
+  }
+  a = ea;
+  b = eb;
 }
 
 TraceScope::~TraceScope() {
-  if (slot < 0) return;
+  if (!a) return;
   std::lock_guard<std::mutex> lk(g_trace_mu);
-  if (slot < (int)g_pending.size()) cudaEventRecord(g_pending[slot].b, st);
+  if (cudaEventRecord(b, st) == cudaSuccess) {
+    g_pending.push_back(TraceRec{name, a, b});
+  } else {
+    g_event_pool.push_back(a);
+    g_event_pool.push_back(b);
+  }
 }
 unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
 void set_cuda_error(cudaError_t e) { g_last_cuda_error = (int)e; }
@@ -271,6 +284,21 @@ int ok_true_residual(const ok_W* W, const void* b, const void* x, double* relres
   return true_residual(W, (const cx<double>*)b, (const cx<double>*)x, relres, (cudaStream_t)stream);
 }
 
+int ok_apply_M_reduce(const ok_W* W, ok_prec prec, int kind, const void* psi, const void* y, void* out, double* sums,
+                      void* stream) {
+  if (!W || !psi || !y || !out || !sums) return OK_EINVAL;
+  const size_t es = prec == OK_F64 ? 16 : (prec == OK_F32 || prec == OK_F32_W16) ? 8 : 0;
+  if (es == 0) return OK_EINVAL;
+  const size_t bytes = (size_t)W->g.V * 12 * es;
+  const char* o = (const char*)out;
+  for (const void* in : {psi, y}) {
+    const char* a = (const char*)in;
+    if (a < o + bytes && o < a + bytes) return OK_EINVAL;
+  }
+  if (((uintptr_t)psi | (uintptr_t)y | (uintptr_t)out) & 15) return OK_EINVAL;
+  return apply_reduce(W, prec, kind, psi, y, out, sums, (cudaStream_t)stream);
+}
+
 int ok_W_expand(const ok_W* W, ok_prec prec, int kind, void* out, void* stream) {
   return expand(W, prec, kind, out, (cudaStream_t)stream);
 }
@@ -294,12 +322,12 @@ int ok_trace_read(ok_trace_stat* stats, int max, int* n) {
     float ms = 0.f;
     cudaError_t e = cudaEventSynchronize(r.b);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
     if (e != cudaSuccess) { set_cuda_error(e); rc = OK_ECUDA; continue; }
     TraceTotals& t = g_totals[r.name];
     t.launches += 1;
     t.ms += ms;
-    g_event_pool.push_back(r.a);
-    g_event_pool.push_back(r.b);
   }
   g_pending.clear();
   int k = 0;

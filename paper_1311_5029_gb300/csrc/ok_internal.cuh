@@ -167,7 +167,7 @@ void set_cuda_error(cudaError_t e);
 struct TraceScope {
   const char* name;
   cudaStream_t st;
-  int slot;
+  cudaEvent_t a, b;  // start and end events; null when this launch is not traced
   TraceScope(const char* n, cudaStream_t s);
   ~TraceScope();
 };

@@ -84,6 +84,8 @@ int expand(const ok_W* W, ok_prec prec, int kind, void* out, cudaStream_t st);
 int bicgstab(const ok_W* W, const cx<double>* b, cx<double>* x, const ok_solve_params* prm, ok_solve_info* info,
              cudaStream_t st);
 int true_residual(const ok_W* W, const cx<double>* b, const cx<double>* x, double* relres, cudaStream_t st);
+int apply_reduce(const ok_W* W, ok_prec prec, int kind, const void* psi, const void* y, void* out, double* sums,
+                 cudaStream_t st);
 int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* b, cx<double>* x, const ok_solve_params* prm, ok_solve_info* info,
                    cudaStream_t st, ok_net* net = nullptr);
 

@@ -352,6 +352,37 @@ int true_residual(const ok_W* W, const cx<double>* bvec, const cx<double>* x, do
   return OK_SUCCESS;
 }
 
+// One application with the fused reduction of a BiCGStab half-iteration (inspection entry
+// ok_apply_M_reduce): kind 1 = EPI_DOT (<y, M psi>), kind 2 = EPI_TS (<M psi, y>, |M psi|^2).
+int apply_reduce(const ok_W* W, ok_prec prec, int kind, const void* psi, const void* y, void* out, double* sums,
+                 cudaStream_t st) {
+  if (!W || !psi || !y || !out || !sums || (kind != 1 && kind != 2)) return OK_EINVAL;
+  if (prec != OK_F64 && prec != OK_F32 && prec != OK_F32_W16) return OK_EINVAL;
+  // The one-thread-per-site FP64 kernel forms <M psi, psi> only.
+  if (prec == OK_F64 && kind == 2 && y != psi) return OK_EINVAL;
+  const int epi = kind == 1 ? EPI_DOT : EPI_TS;
+  Workspace ws;
+  ws.st = st;
+  cudaError_t err = cudaSuccess;
+  double* part = ws.get<double>((size_t)apply_blocks_needed(W) * 4, &err);
+  SolverState* dst = ws.get<SolverState>(1, &err);
+  HostState hs;
+  if (!part || !dst || !hs.h) { if (err != cudaSuccess) set_cuda_error(err); return OK_ENOMEM; }
+  OK_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(SolverState), st));
+  const RedArgs ra{dst, part, nullptr, FIN_NONE};
+  if (prec == OK_F64) {
+    EpiArgs<double> e{(const cx<double>*)y, nullptr, ra, &dst->ticket[0], nullptr};
+    OK_TRY(launch_apply<double>(W, (const cx<double>*)psi, (cx<double>*)out, epi, e, st));
+  } else {
+    EpiArgs<float> e{(const cx<float>*)y, nullptr, ra, &dst->ticket[0], nullptr};
+    if (prec == OK_F32) OK_TRY(launch_apply<float>(W, (const cx<float>*)psi, (cx<float>*)out, epi, e, st));
+    else OK_TRY(launch_apply_w16(W, (const cx<float>*)psi, (cx<float>*)out, epi, e, st));
+  }
+  OK_TRY(read_state(dst, hs.h, st));
+  for (int k = 0; k < 3; ++k) sums[k] = kind == 1 && k == 2 ? 0.0 : hs.h->aux[k];
+  return OK_SUCCESS;
+}
+
 }  // namespace okgb
 
 // ============================================================================ multi right-hand side

@@ -3,13 +3,16 @@
 // The reduction scratch (per-block partial sums, the completion ticket and the final sums) lives
 // in one file-scope __device__ array of fixed size instead of memory obtained from cudaMalloc.
 // Every GPU that loads this library holds the array until the process exits.  Host code cannot
-// use the array's name as a device address, so the address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) and passed to the kernel.
+// use the array's name as a device address, so every call looks the address up with
+// cudaGetSymbolAddress, with the caller's device current, and passes it to the kernel.  The
+// lookup allocates nothing; doing it on every call (rather than caching it per device ordinal)
+// keeps the address right after a device reset or when another context has loaded the module at
+// a different address.  The first call on a device may load the module there, so it should come
+// before any stream capture.
 #include "ok_launch.cuh"
 
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 namespace okgb {
 namespace {
@@ -23,22 +26,11 @@ constexpr size_t kScratchBytes = kStateBytes + kPartialDoubles * sizeof(double);
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device, looked up on first use.
+// Device address of g_scratch in the current context.
 int scratch_address(void** out) {
-  int dev = 0;
-  OK_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return OK_EINVAL;
-  std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    OK_CUDA_TRY(cudaGetSymbolAddress(&p, g_scratch));
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  void* p = nullptr;
+  OK_CUDA_TRY(cudaGetSymbolAddress(&p, g_scratch));
+  *out = p;
   return OK_SUCCESS;
 }
 

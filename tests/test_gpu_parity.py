@@ -72,6 +72,41 @@ def test_apply_fp32(case):
     got = ok.apply_M(W, to_dev(psi)).cpu().numpy()
     exp = wform.apply(U, c, psi.astype(np.complex128), bc)
     assert rel_l2(got, exp) < FP32_TOL
+    assert rel_max(got, exp) < FP32_TOL
+
+
+@pytest.mark.parametrize("case", SMALL_CASES[:5], ids=CASE_IDS[:5])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32_w16"])
+def test_fused_reduction_applies(case, prec):
+    """The launches a BiCGStab iteration runs (v = M p with <rhat, v>; t = M s with <t, s>, <t, t>):
+    their output vectors and their fused inner products against the oracle's M psi and numpy's
+    inner products of it."""
+    _, dims, bc, eps, c = case
+    U = synth.random_links(dims, eps, 4200 + sum(dims))
+    psi = synth.gaussian_source(dims, 4300 + sum(dims))
+    y = synth.gaussian_source(dims, 4400 + sum(dims))
+    W = ok.precompute_W(to_dev(U), c, bc, ok.W_F64 | ok.W_F32 | ok.W_F16)
+    if prec == "f64":
+        tol, p, dt = FP64_TOL, ok.F64, np.complex128
+    else:
+        tol, p, dt = (FP32_TOL, ok.F32, np.complex64) if prec == "f32" else (4 * 2.0 ** -11, ok.F32_W16, np.complex64)
+        psi, y = psi.astype(dt), y.astype(dt)
+    exp = wform.apply(U, c, psi.astype(np.complex128), bc)
+    yd, pd = to_dev(y), to_dev(psi)
+    out, (dot, _) = ok.apply_M_reduce(W, pd, yd, ok.REDUCE_DOT, prec=p)
+    got = out.cpu().numpy()
+    assert rel_l2(got, exp) < tol and rel_max(got, exp) < tol
+    scale = np.linalg.norm(y) * np.linalg.norm(exp)
+    assert abs(dot - np.vdot(y.astype(np.complex128), exp)) < tol * scale
+    # <t, s> with s = psi (the unpreconditioned iteration) and, except for the FP64 kernel, a
+    # separate y (the right-preconditioned iteration takes <t, s> against s while t = M (P s))
+    for second in ([pd] if prec == "f64" else [pd, yd]):
+        out, (ts, tt) = ok.apply_M_reduce(W, pd, second, ok.REDUCE_TS, prec=p)
+        got = out.cpu().numpy()
+        sv = second.cpu().numpy().astype(np.complex128)
+        assert rel_l2(got, exp) < tol
+        assert abs(ts - np.vdot(exp, sv)) < tol * np.linalg.norm(exp) * np.linalg.norm(sv)
+        assert abs(tt - np.vdot(exp, exp).real) < 2 * tol * np.vdot(exp, exp).real
 
 
 def test_links_in_fp32():
@@ -119,6 +154,7 @@ def test_full_size_16cube32_sampled():
     got32 = ok.apply_M(W, to_dev(src.astype(np.complex64))).cpu().numpy().reshape(V, 4, 3)[sites]
     assert rel_max(got64, exp) < 10 * FP64_TOL
     assert rel_l2(got32, exp) < FP32_TOL
+    assert rel_max(got32, exp) < FP32_TOL
     assert abs(W.u0 - gauge.tadpole_u0(U)) < 1e-13
     # the handle holds 43 colour matrices per site in each precision
     assert W.nbytes == ((V + 31) // 32) * 32 * 43 * 9 * (16 + 8)
