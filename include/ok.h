@@ -51,8 +51,10 @@ typedef struct {
 #define OK_MAX_SITES (1 << 27)
 
 /* Precision of an application of M: OK_F64 (complex128 fields, FP64-accurate W), OK_F32 (complex64
- * fields, FP32 W) or OK_F32_W16 (complex64 fields and FP32 arithmetic with the FP16 copy of W). */
-typedef enum { OK_F64 = 0, OK_F32 = 1, OK_F32_W16 = 2 } ok_prec;
+ * fields, FP32 W), OK_F32_W16 (complex64 fields and FP32 arithmetic with the FP16 copy of W) or
+ * OK_F16_TC (several right-hand sides at once on the tensor cores: complex64 fields and the
+ * OK_W_F16_TC copy of W enter the products as FP16, which accumulate in FP32). */
+typedef enum { OK_F64 = 0, OK_F32 = 1, OK_F32_W16 = 2, OK_F16_TC = 3 } ok_prec;
 
 /* Which stored copies a W handle carries (bit mask for ok_precompute_W).  OK_W_DF64 keeps FP64
  * accuracy as double-float pairs (hi + lo, two floats, about 48 significand bits): FP64 applications
@@ -66,6 +68,11 @@ typedef enum { OK_F64 = 0, OK_F32 = 1, OK_F32_W16 = 2 } ok_prec;
 #define OK_W_DF64 4
 #define OK_W_F16 8   /* half-precision copy (relative rounding 2^-11) for the low-precision iteration */
 #define OK_W_LINKS 16 /* also keep an FP32 copy of the links (for the learned preconditioner, ok_net_*) */
+/* FP16 copy for the tensor-core multi-right-hand-side apply (OK_F16_TC): per site, the operator's
+ * hops written as 6x6 complex blocks acting on the spin projections (u + l) / sqrt 2 and
+ * (u - l) / sqrt 2 of the neighbour spinor, each entry rounded once from FP64 (relative 2^-11);
+ * 3216 bytes per site, in a site-major layout. */
+#define OK_W_F16_TC 32
 
 /* Coefficients of the tree-level, tadpole-improved OK action (Sec. 1; they enter the W formulas,
  * Eqs. shifted_W_first .. shifted_W_last).  u0 <= 0: u0 is computed from the mean plaquette of
@@ -89,6 +96,7 @@ typedef struct {
 #define OK_SOLVE_F64    1  /* plain FP64 BiCGStab (needs OK_W_F64) */
 #define OK_SOLVE_MIXED  2  /* FP32 BiCGStab with FP64 reliable updates (needs both precisions) */
 #define OK_SOLVE_MIXED16 3 /* as OK_SOLVE_MIXED with the FP16 W copy in the FP32 iteration (OK_W_F16) */
+#define OK_SOLVE_MIXED_TC 4 /* ok_bicgstab_multi: as OK_SOLVE_MIXED with the tensor-core apply (OK_W_F16_TC) */
 
 typedef struct {
     double tol;          /* stop when |b - M x| / |b| < tol (true FP64 residual) */
@@ -109,7 +117,8 @@ typedef struct ok_net ok_net;  /* opaque, library-owned learned preconditioner (
  * and the forward set W^0_x, W^+_{mu,x}, W^{++}_{ii,x}, W^{++}_{ij,x}, W^{+-}_{ij,x} (i < j) per
  * site, unshifted, in a private site-blocked layout.  The backward matrices are not stored: they
  * follow from the forward ones by Eqs. conjugate and opp_diag_pre_mat.  Arithmetic is FP64;
- * W_precs selects the stored copies (at least one of OK_W_F64, OK_W_F32, OK_W_DF64, OK_W_F16),
+ * W_precs selects the stored copies (at least one of OK_W_F64, OK_W_F32, OK_W_DF64, OK_W_F16,
+ * OK_W_F16_TC),
  * plus OK_W_LINKS to keep an FP32 copy of the links in the handle.
  *   links: device [T][Z][Y][X][4][3][3] complex in links_prec; not retained after the call.
  *   W_out: receives a new handle owned by the caller, released with ok_free_W.
@@ -155,16 +164,26 @@ int ok_bicgstab_ex(const ok_W* W, const void* src, void* x, const ok_solve_param
 /* Several right-hand sides at once (the 12 spin-colour sources of a propagator; the paper's
  * method solves one source at a time, Sec. 2.3).
  *
- * ok_apply_M_multi: out_k = M psi_k for k < nrhs in one launch; every W matrix a thread loads is
- * applied to several right-hand sides (the count chosen by ok_autotune).  prec OK_F32 (FP32 W) or
- * OK_F32_W16 (FP16 W), FP32 fields and arithmetic.
+ * ok_apply_M_multi: out_k = M psi_k for k < nrhs in one launch.  prec OK_F32 (FP32 W) or
+ * OK_F32_W16 (FP16 W): FP32 fields and arithmetic, every W matrix a thread loads applied to several
+ * right-hand sides (the count chosen by ok_autotune).  prec OK_F16_TC (needs OK_W_F16_TC, nrhs <= 16):
+ * on the tensor cores; per site and hop the right-hand sides times the hop's 6x6 spin-projected
+ * blocks is a complex GEMM (warp-level mma.sync m16n8k16, FP16 operands, FP32 accumulation).  Each
+ * right-hand side enters as FP16 scaled by a power of two that puts its largest component below
+ * 2^14, so fields of any magnitude keep FP16's relative precision (components below 2^-24 of the
+ * largest flush to zero); the result is FP32.  This entry converts to and from the private field
+ * layout of the tensor-core kernel around the launch, in stream-ordered scratch.
  *   psi, out: device [nrhs][V][4][3] complex64, 16-byte aligned, not overlapping.
- * Errors: OK_EINVAL (null, nrhs < 1, overlap, misalignment, copy missing), OK_ECUDA.  Asynchronous.
+ * Errors: OK_EINVAL (null, nrhs < 1 or > 16 for OK_F16_TC, overlap, misalignment, copy missing),
+ * OK_ENOMEM, OK_ECUDA.  Asynchronous.
  *
  * ok_bicgstab_multi: solves M x_k = src_k for k < nrhs with the mixed-precision method of
  * ok_bicgstab_ex run for all systems in lockstep: FP32 iteration on the FP32 (OK_SOLVE_MIXED) or
- * FP16 (OK_SOLVE_MIXED16; OK_SOLVE_AUTO picks it when the handle has OK_W_F16) copy of W with
- * FP64 reliable updates, every system to its own true FP64 residual below params->tol.  One
+ * FP16 (OK_SOLVE_MIXED16) copy of W, or on the tensor cores (OK_SOLVE_MIXED_TC: FP32 iteration
+ * vectors in the tensor-core kernel's layout, FP16 copies of the applied vectors scaled per system
+ * from its residual norm, nrhs <= 16), with FP64 reliable updates, every system to its own true
+ * FP64 residual below params->tol.  OK_SOLVE_AUTO picks OK_SOLVE_MIXED_TC when the handle has
+ * OK_W_F16_TC and nrhs <= 16, else OK_SOLVE_MIXED16 when it has OK_W_F16, else OK_SOLVE_MIXED.  One
  * iteration is five launches for all systems, captured once into a CUDA graph and replayed
  * params->check_every iterations at a time.
  *   src, x: device [nrhs][V][4][3] complex128 (x: initial guess in, solution out), 1 <= nrhs <= 64;
@@ -288,8 +307,9 @@ int ok_true_residual_static(const ok_W* W, const void* b, const void* x, void* r
                             void* stream);
 
 /* Inspection: write the dense 12x12 forward matrix of one kind for every site, reconstructed from
- * the stored representation of precision `prec` (OK_F32_W16: the half-precision copy; OK_F64 reads
- * OK_W_F64, else OK_W_DF64): out = device [V][12][12] complex128 (row index
+ * the stored representation of precision `prec` (OK_F32_W16: the half-precision copy; OK_F16_TC: the
+ * tensor-core copy's blocks, W = T Q T / 2; OK_F64 reads OK_W_F64, else OK_W_DF64):
+ * out = device [V][12][12] complex128 (row index
  * 3*spin + colour).  kind: 0 W^0; 1..4 W^+_mu (x, y, z, t); 5..7 W^{++}_ii (x, y, z);
  * 8..10 W^{++}_ij (xy, xz, yz); 11..13 W^{+-}_ij (xy, xz, yz; they multiply psi_{x+i-j}). */
 int ok_W_expand(const ok_W* W, ok_prec prec, int kind, void* out, void* stream);

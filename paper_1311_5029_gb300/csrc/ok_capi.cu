@@ -106,7 +106,7 @@ void ok_free_W(ok_W* W) {
   if (!W) return;
   // Returned to the stream-ordered pool they came from, after the work already queued on the
   // legacy default stream (the caller guarantees that no work on the handle is pending).
-  for (void* q : {W->W64, W->W32, W->Wdf, W->W16, W->L32})
+  for (void* q : {W->W64, W->W32, W->Wdf, W->W16, W->L32, W->Wtc})
     if (q) cudaFreeAsync(q, 0);
   delete W;
 }
@@ -179,12 +179,37 @@ int ok_bicgstab_ex(const ok_W* W, const void* src, void* x, const ok_solve_param
 }
 
 int ok_apply_M_multi(const ok_W* W, ok_prec prec, int nrhs, const void* psi, void* out, void* stream) {
-  if (!W || !psi || !out || nrhs < 1 || (prec != OK_F32 && prec != OK_F32_W16)) return OK_EINVAL;
+  if (!W || !psi || !out || nrhs < 1 || (prec != OK_F32 && prec != OK_F32_W16 && prec != OK_F16_TC)) return OK_EINVAL;
   const size_t bytes = (size_t)W->g.V * 12 * 8 * nrhs;
   const char* a = (const char*)psi;
   const char* b = (const char*)out;
   if (a < b + bytes && b < a + bytes) return OK_EINVAL;
   if (((uintptr_t)psi | (uintptr_t)out) & 15) return OK_EINVAL;
+  if (prec == OK_F16_TC) {
+    // canonical layout -> the FP16 tensor-core layout (scaled per right-hand side), apply, and back;
+    // stream-ordered scratch
+    if (!W->Wtc || nrhs > 16) return OK_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)W->g.V * 12 * nrhs;  // complex numbers
+    char* scratch = nullptr;
+    const size_t o16 = 0, o32 = tc_in16_bytes(W->g.V), oam = o32 + n * 8, oinv = oam + 64;
+    OK_CUDA_TRY(cudaMallocAsync((void**)&scratch, oinv + 64, st));
+    unsigned* amax = (unsigned*)(scratch + oam);
+    float* inv = (float*)(scratch + oinv);
+    int rc = launch_to_tc16((const cx<float>*)psi, scratch + o16, W->g.V, nrhs, amax, inv, st);
+    if (rc == OK_SUCCESS) {
+      TcEpi ep{};
+      ep.inv_scale = inv;
+      rc = launch_apply_tc(W, scratch + o16, (cx<float>*)(scratch + o32), nrhs, EPI_NONE, ep, st);
+    }
+    if (rc == OK_SUCCESS) rc = launch_from_tc((const cx<float>*)(scratch + o32), (cx<float>*)out, W->g.V, nrhs, st);
+    const cudaError_t fe = cudaFreeAsync(scratch, st);
+    if (rc == OK_SUCCESS && fe != cudaSuccess) {
+      set_cuda_error(fe);
+      rc = OK_ECUDA;
+    }
+    return rc;
+  }
   const bool w16 = prec == OK_F32_W16;
   if ((w16 && !W->W16) || (!w16 && !W->W32)) return OK_EINVAL;
   MultiEpi e{};

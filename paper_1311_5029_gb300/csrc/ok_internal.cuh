@@ -196,6 +196,7 @@ struct ok_W {
   void* Wdf;     // cx<dd>[...]: FP64-accurate double-float copy
   void* W16;     // cx<__half>[...]: half-precision copy
   void* L32;     // cx<float>[nblk][4][9][32]: FP32 links, site-blocked (OK_W_LINKS), for the preconditioner network
+  void* Wtc;     // [V][804] FP16 complex words: blocks of the tensor-core apply (OK_W_F16_TC, ok_tc.cu)
   size_t bytes;
   int device;
   mutable okgb::Tune tune;

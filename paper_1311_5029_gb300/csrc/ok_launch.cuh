@@ -46,6 +46,40 @@ int launch_apply_multi(const ok_W* W, bool w16, const cx<float>* psi, cx<float>*
                        const MultiShape& shape, cudaStream_t st);
 int mrhs_blocks_needed(const ok_W* W);  // upper bound of the grid width
 MultiShape multi_shape(const ok_W* W, bool w16, int nrhs);  // tuned or default
+// Tensor-core multi right-hand side apply (ok_tc.cu).  Fields in the tensor-core layout: float4 unit
+// ((site * 2 + b) * nrhs + r) * 3 + c holds the projection h_b (b = +, -) of right-hand side r at
+// colour c, spins 0 and 1; nrhs <= 16.
+struct TcEpi {
+  const float4* y;     // EPI_DOT: rhat (<y, out>); EPI_TS: the y of <out, y> (null: the input)
+  SolverState* st;     // [nrhs]
+  double* part;        // partials of right-hand side r at part + r * pstride (pstride >= 3 * grid)
+  long long pstride;
+  unsigned* ticket;    // grid completion counter (zero between launches)
+  int fin;             // FIN_ALPHA (EPI_DOT) or FIN_OMEGA (EPI_TS)
+  const float* inv_scale;  // [nrhs] 1 / sigma of the FP16 inputs; null: from each system's |r| (st)
+};
+int launch_tc_build(const ok_W* W, const cx<double>* W64, const WScalars* dsc, cudaStream_t st);
+size_t tc_record_bytes();
+int launch_tc_expand(const ok_W* W, int kind, cx<double>* out, cudaStream_t st);
+int tc_blocks_needed(const ok_W* W);
+int tc_vec_blocks(int nrhs);
+int launch_apply_tc(const ok_W* W, const void* in16, cx<float>* out, int nrhs, int epi, const TcEpi& ep, cudaStream_t st);
+// canonical complex64 [nrhs][V][4][3] -> FP16 tensor-core layout with a power-of-two scale per right-hand
+// side (amax: nrhs words of scratch; inv_scale: nrhs floats out, 1 / sigma); FP32 tensor-core layout -> canonical.
+size_t tc_in16_bytes(int V);  // the FP16 input layout of the tensor-core apply (768 bytes per site)
+int launch_to_tc16(const cx<float>* in, void* out16, int V, int nrhs, unsigned* amax, float* inv_scale, cudaStream_t st);
+int launch_from_tc(const cx<float>* in, cx<float>* out, int V, int nrhs, cudaStream_t st);
+int launch_tc_update_s(const cx<float>* r, const cx<float>* v, cx<float>* s, void* s16, int V, int nrhs, const SolverState* st,
+                       cudaStream_t strm);
+int launch_tc_update_p(cx<float>* p, void* p16, const cx<float>* r, const cx<float>* v, int V, int nrhs, const SolverState* st,
+                       int only, cudaStream_t strm);
+int launch_tc_half(const cx<float>* p, void* p16, int V, int nrhs, const SolverState* st, int only, cudaStream_t strm);
+int launch_tc_update_xr(cx<float>* x, const void* p16, const cx<float>* s, const void* s16, const cx<float>* t, cx<float>* r,
+                        const cx<float>* rhat, int V, int nrhs, SolverState* st, double* part, long long pstride,
+                        unsigned* ticket, cudaStream_t strm);
+int launch_tc_demote(const cx<double>* r64, cx<float>* r, cx<float>* rhat, cx<float>* p, int V, int nrhs, int k, bool restart,
+                     SolverState* st, double* part, cudaStream_t strm);
+int launch_tc_accum(cx<double>* x64, cx<float>* x, int V, int nrhs, int k, cudaStream_t strm);
 // FP64 complex -> double-float complex (n complex numbers).
 int launch_to_df(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t st);
 

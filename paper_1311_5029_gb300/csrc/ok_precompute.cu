@@ -485,7 +485,7 @@ int geom_from_lattice(const ok_lattice* lat, Geom* g) { return check_lattice(lat
 
 template <typename LT>
 static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaStream_t st,
-                          cx<double>* EB, double* part, WScalars* dsc) {
+                          cx<double>* EB, double* part, WScalars* dsc, cx<double>* W64tmp) {
   const Geom& g = W->g;
   const cx<LT>* U = (const cx<LT>*)links;
   int nb1 = grid_for(g.V, K1_THREADS);
@@ -499,7 +499,7 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
     scalars_kernel<<<1, 256, 0, st>>>(part, nb1, g, *c, dsc);
   }
   OK_LAUNCH_CHECK();
-  WOut o{(cx<double>*)W->W64, (cx<float>*)W->W32, (cx<dd>*)W->Wdf, (cx<__half>*)W->W16};
+  WOut o{W->W64 ? (cx<double>*)W->W64 : W64tmp, (cx<float>*)W->W32, (cx<dd>*)W->Wdf, (cx<__half>*)W->W16};
   int nb2 = grid_for(g.V, K2_THREADS);
   for (int part_id = 0; part_id < 5; ++part_id) {
     {
@@ -546,8 +546,8 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
                int precs, cudaStream_t st, ok_W** W_out) {
   if (!lat || !links || !c || !W_out) return OK_EINVAL;
   if (links_prec != OK_F64 && links_prec != OK_F32) return OK_EINVAL;
-  if ((precs & (OK_W_F64 | OK_W_F32 | OK_W_DF64 | OK_W_F16)) == 0 ||
-      (precs & ~(OK_W_F64 | OK_W_F32 | OK_W_DF64 | OK_W_F16 | OK_W_LINKS)))
+  if ((precs & (OK_W_F64 | OK_W_F32 | OK_W_DF64 | OK_W_F16 | OK_W_F16_TC)) == 0 ||
+      (precs & ~(OK_W_F64 | OK_W_F32 | OK_W_DF64 | OK_W_F16 | OK_W_LINKS | OK_W_F16_TC)))
     return OK_EINVAL;
   if (!(c->u0 > 0.0) && c->u0 > 0.0) return OK_EINVAL;
   *W_out = nullptr;
@@ -568,8 +568,9 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
   cx<double>* EB = nullptr;
   double* part = nullptr;
   WScalars* dsc = nullptr;
+  void* W64tmp = nullptr;  // FP64 matrices for the tensor-core copy when OK_W_F64 is not kept
   auto fail = [&](int code) {
-    for (void* q : {(void*)EB, (void*)part, (void*)dsc, W->W64, W->W32, W->Wdf, W->W16, W->L32})
+    for (void* q : {(void*)EB, (void*)part, (void*)dsc, W64tmp, W->W64, W->W32, W->Wdf, W->W16, W->L32, W->Wtc})
       if (q) cudaFreeAsync(q, st);
     delete W;
     return code;
@@ -599,6 +600,14 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
     e = cudaMemsetAsync(static_cast<cx<__half>*>(W->W16) + tail, 0, (elems - tail) * sizeof(cx<__half>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
   }
+  if (precs & OK_W_F16_TC) {
+    e = cudaMallocAsync(&W->Wtc, (size_t)g.V * tc_record_bytes(), st);
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
+    if (!(precs & OK_W_F64)) {
+      e = cudaMallocAsync(&W64tmp, elems * sizeof(cx<double>), st);
+      if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
+    }
+  }
   const size_t nlink = (size_t)g.nblk * LANES * 4 * 9;  // blocked: whole 32-site blocks
   if (precs & OK_W_LINKS) {
     e = cudaMallocAsync(&W->L32, nlink * sizeof(cx<float>), st);
@@ -616,7 +625,7 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
   }
   W->bytes = (W->W64 ? elems * sizeof(cx<double>) : 0) + (W->W32 ? elems * sizeof(cx<float>) : 0) +
              (W->Wdf ? elems * sizeof(cx<dd>) : 0) + (W->W16 ? elems * sizeof(cx<__half>) : 0) +
-             (W->L32 ? nlink * sizeof(cx<float>) : 0);
+             (W->L32 ? nlink * sizeof(cx<float>) : 0) + (W->Wtc ? (size_t)g.V * tc_record_bytes() : 0);
   int nb1 = grid_for(g.V, K1_THREADS);
   e = cudaMallocAsync((void**)&EB, (size_t)g.V * 6 * 9 * sizeof(cx<double>), st);
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
@@ -624,9 +633,13 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
   e = cudaMallocAsync((void**)&dsc, sizeof(WScalars), st);
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
-  rc = links_prec == OK_F64 ? run_precompute<double>(W, links, c, st, EB, part, dsc)
-                            : run_precompute<float>(W, links, c, st, EB, part, dsc);
+  rc = links_prec == OK_F64 ? run_precompute<double>(W, links, c, st, EB, part, dsc, (cx<double>*)W64tmp)
+                            : run_precompute<float>(W, links, c, st, EB, part, dsc, (cx<double>*)W64tmp);
   if (rc != OK_SUCCESS) return fail(rc);
+  if (W->Wtc) {
+    rc = launch_tc_build(W, W->W64 ? (const cx<double>*)W->W64 : (const cx<double>*)W64tmp, dsc, st);
+    if (rc != OK_SUCCESS) return fail(rc);
+  }
   e = cudaMemcpyAsync(&W->sc, dsc, sizeof(WScalars), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
   e = cudaStreamSynchronize(st);
@@ -634,13 +647,15 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
   cudaFreeAsync(EB, st);
   cudaFreeAsync(part, st);
   cudaFreeAsync(dsc, st);
-  EB = nullptr; part = nullptr; dsc = nullptr;
+  if (W64tmp) cudaFreeAsync(W64tmp, st);
+  EB = nullptr; part = nullptr; dsc = nullptr; W64tmp = nullptr;
   *W_out = W;
   return OK_SUCCESS;
 }
 
 int expand(const ok_W* W, ok_prec prec, int kind, void* out, cudaStream_t st) {
   if (!W || !out || kind < 0 || kind > 13) return OK_EINVAL;
+  if (prec == OK_F16_TC) return launch_tc_expand(W, kind, (cx<double>*)out, st);
   const void* src = prec == OK_F64 ? (W->W64 ? W->W64 : W->Wdf) : prec == OK_F32 ? W->W32 : prec == OK_F32_W16 ? W->W16 : nullptr;
   if (!src) return OK_EINVAL;
   WScalars* dsc = nullptr;

@@ -401,10 +401,15 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
   if (!(prm->tol > 0.0) || prm->maxiter < 1 || prm->max_restarts < 0 || prm->check_every < 1) return OK_EINVAL;
   if (!(prm->delta > 0.0 && prm->delta < 1.0)) return OK_EINVAL;
   int mode = prm->mode;
-  if (mode == OK_SOLVE_AUTO) mode = W->W16 ? OK_SOLVE_MIXED16 : OK_SOLVE_MIXED;
-  if (mode != OK_SOLVE_MIXED && mode != OK_SOLVE_MIXED16) return OK_EINVAL;
+  if (mode == OK_SOLVE_AUTO)
+    mode = (W->Wtc && nrhs <= 16 && !net) ? OK_SOLVE_MIXED_TC : W->W16 ? OK_SOLVE_MIXED16 : OK_SOLVE_MIXED;
+  if (mode != OK_SOLVE_MIXED && mode != OK_SOLVE_MIXED16 && mode != OK_SOLVE_MIXED_TC) return OK_EINVAL;
+  // Tensor-core form: iteration vectors in the tensor-core layout (ok_tc.cu), applies on the
+  // tensor cores; the network preconditioner works on the canonical layout and is not combined.
+  const bool tcp = mode == OK_SOLVE_MIXED_TC;
+  if (tcp && (!W->Wtc || nrhs > 16 || net)) return OK_EINVAL;
   const bool w16 = mode == OK_SOLVE_MIXED16;
-  if ((w16 && !W->W16) || (!w16 && !W->W32) || !(W->W64 || W->Wdf)) return OK_EINVAL;
+  if ((w16 && !W->W16) || (!w16 && !tcp && !W->W32) || !(W->W64 || W->Wdf)) return OK_EINVAL;
   if ((const void*)bvec == (const void*)x) return OK_EINVAL;
   if (net && !W->L32) return OK_EINVAL;  // the network needs the handle's FP32 links
 
@@ -445,9 +450,24 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
   long long maxblocks = mrhs_blocks_needed(W);
   if (blas_blocks(n) > maxblocks) maxblocks = blas_blocks(n);
   if (blas_blocks(n / 2) > maxblocks) maxblocks = blas_blocks(n / 2);
+  if (tcp) {
+    for (long long nb : {(long long)tc_blocks_needed(W), (long long)tc_vec_blocks(nrhs), (long long)blas_blocks(3LL * W->g.V)})
+      if (nb > maxblocks) maxblocks = nb;
+  }
   const long long pstride = 4 * maxblocks;
   double* part = ws.get<double>((size_t)pstride * nrhs, &err);
   SolverState* dst = ws.get<SolverState>(nrhs, &err);
+  unsigned* tickets = tcp ? ws.get<unsigned>(4, &err) : nullptr;  // grid completion counters of the TC kernels
+  // FP16 copies of p and s (scaled per system) that the tensor-core apply reads
+  unsigned char* p16 = tcp ? ws.get<unsigned char>(tc_in16_bytes(W->g.V), &err) : nullptr;
+  unsigned char* s16 = tcp ? ws.get<unsigned char>(tc_in16_bytes(W->g.V), &err) : nullptr;
+  if (tcp && (!tickets || !p16 || !s16)) { set_cuda_error(err); return OK_ENOMEM; }
+  if (tcp) {  // the slots of absent right-hand sides stay zero
+    OK_CUDA_TRY(cudaMemsetAsync(p16, 0, tc_in16_bytes(W->g.V), st));
+    OK_CUDA_TRY(cudaMemsetAsync(s16, 0, tc_in16_bytes(W->g.V), st));
+  }
+  if (tcp) OK_CUDA_TRY(cudaMemsetAsync(tickets, 0, 4 * sizeof(unsigned), st));
+  const int V = W->g.V;
   cx<double>* r64 = ws.get<cx<double>>(n, &err);
   cx<dd>* xdf = W->Wdf ? ws.get<cx<dd>>(n, &err) : nullptr;
   IterBufs<float> b{};
@@ -495,8 +515,10 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
       inf[k].fp64_applies++;
       r0 = r64;
     }
-    OK_TRY(launch_demote(r0, vec(b.r, k), vec(b.rhat, k), vec(b.p, k), n, true, &dst[k], part, st));
+    if (tcp) OK_TRY(launch_tc_demote(r0, b.r, b.rhat, b.p, V, nrhs, k, true, &dst[k], part, st));
+    else OK_TRY(launch_demote(r0, vec(b.r, k), vec(b.rhat, k), vec(b.p, k), n, true, &dst[k], part, st));
   }
+  if (tcp) OK_TRY(launch_tc_half(b.p, p16, V, nrhs, dst, -1, st));
   OK_CUDA_TRY(cudaMemcpyAsync(h, dst, sizeof(SolverState) * nrhs, cudaMemcpyDeviceToHost, st));
   OK_CUDA_TRY(cudaStreamSynchronize(st));
   for (int k = 0; k < nrhs; ++k) {
@@ -514,6 +536,15 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
   // One iteration for every system; with a right preconditioner P (one launch per network layer
   // for all systems) the operator is M P, as in iterate() above.
   auto iterate_all = [&]() -> int {
+    if (tcp) {
+      const TcEpi e1{(const float4*)b.rhat, dst, part, pstride, tickets + 0, FIN_ALPHA, nullptr};
+      OK_TRY(launch_apply_tc(W, p16, b.v, nrhs, EPI_DOT, e1, st));
+      OK_TRY(launch_tc_update_s(b.r, b.v, b.s, s16, V, nrhs, dst, st));
+      const TcEpi e2{(const float4*)b.s, dst, part, pstride, tickets + 1, FIN_OMEGA, nullptr};
+      OK_TRY(launch_apply_tc(W, s16, b.t, nrhs, EPI_TS, e2, st));
+      OK_TRY(launch_tc_update_xr(b.x, p16, b.s, s16, b.t, b.r, b.rhat, V, nrhs, dst, part, pstride, tickets + 2, st));
+      return launch_tc_update_p(b.p, p16, b.r, b.v, V, nrhs, dst, -1, st);
+    }
     const cx<float>* pin = b.p;
     const cx<float>* sin = b.s;
     if (net) {
@@ -579,7 +610,8 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
       if (halt == HALT_NONE) continue;
       if (halt == HALT_NONFINITE) { status[k] = OK_ENONFINITE; continue; }
       // fold the FP32 increment into x and recompute the true residual in FP64
-      OK_TRY(launch_accum_x(vec(x, k), vec(b.x, k), n, st));
+      if (tcp) OK_TRY(launch_tc_accum(vec(x, k), b.x, V, nrhs, k, st));
+      else OK_TRY(launch_accum_x(vec(x, k), vec(b.x, k), n, st));
       OK_TRY(residual64(W, vec(bvec, k), vec(x, k), r64, &dst[k], part, xdf, st));
       inf[k].fp64_applies++;
       OK_TRY(read_state(&dst[k], &h[k], st));
@@ -589,8 +621,13 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
       if (halt == HALT_MAXITER || h[k].iter >= prm->maxiter) { status[k] = OK_ENOCONV; OK_CUDA_TRY(freeze(k)); continue; }
       if (halt == HALT_UPDATE) {
         inf[k].reliable_updates++;
-        OK_TRY(launch_demote(r64, vec(b.r, k), vec(b.rhat, k), vec(b.p, k), n, false, &dst[k], part, st));
-        OK_TRY(launch_update_p<float>(vec(b.p, k), vec(b.r, k), vec(b.v, k), n, &dst[k], st));
+        if (tcp) {
+          OK_TRY(launch_tc_demote(r64, b.r, b.rhat, b.p, V, nrhs, k, false, &dst[k], part, st));
+          OK_TRY(launch_tc_update_p(b.p, p16, b.r, b.v, V, nrhs, dst, k, st));
+        } else {
+          OK_TRY(launch_demote(r64, vec(b.r, k), vec(b.rhat, k), vec(b.p, k), n, false, &dst[k], part, st));
+          OK_TRY(launch_update_p<float>(vec(b.p, k), vec(b.r, k), vec(b.v, k), n, &dst[k], st));
+        }
         continue;
       }
       if (inf[k].restarts >= prm->max_restarts) {
@@ -599,7 +636,12 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
         continue;
       }
       inf[k].restarts++;
-      OK_TRY(launch_demote(r64, vec(b.r, k), vec(b.rhat, k), vec(b.p, k), n, true, &dst[k], part, st));
+      if (tcp) {
+        OK_TRY(launch_tc_demote(r64, b.r, b.rhat, b.p, V, nrhs, k, true, &dst[k], part, st));
+        OK_TRY(launch_tc_half(b.p, p16, V, nrhs, dst, k, st));
+      } else {
+        OK_TRY(launch_demote(r64, vec(b.r, k), vec(b.rhat, k), vec(b.p, k), n, true, &dst[k], part, st));
+      }
     }
   }
   OK_CUDA_TRY(cudaMemcpyAsync(h, dst, sizeof(SolverState) * nrhs, cudaMemcpyDeviceToHost, st));

@@ -80,6 +80,31 @@ def random_links(dims, eps: float, seed: int) -> np.ndarray:
     return random_su3(lattice_shape(dims) + (4,), eps, seed)
 
 
+def device_random_links(dims, eps: float, seed: int, device="cuda"):
+    """The distribution of `random_links` drawn on a CUDA device with torch's seeded generator
+    (for lattices where the host generator takes minutes): A with iid N(0, 1) real and imaginary
+    entries, H = (A + A^dag) / 2 - tr / 3, U = exp(i eps H) (torch's batched matrix exponential;
+    the host recipe's eigendecomposition gives the same matrix up to rounding).  Returns a
+    [T][Z][Y][X][4][3][3] complex128 tensor on the device; the bits differ from `random_links` for
+    the same seed."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    shape = lattice_shape(dims) + (4,)
+    n = int(np.prod(shape))
+    out = torch.empty((n, 3, 3), dtype=torch.complex128, device=device)
+    chunk = 1 << 18
+    eye = torch.eye(3, dtype=torch.complex128, device=device)
+    for s0 in range(0, n, chunk):
+        m = min(chunk, n - s0)
+        a = torch.view_as_complex(torch.randn((m, 3, 3, 2), generator=g, device=device, dtype=torch.float64))
+        h = 0.5 * (a + a.conj().transpose(-1, -2))
+        tr = torch.diagonal(h, dim1=-2, dim2=-1).sum(-1).real / 3.0
+        h = h - tr[:, None, None] * eye
+        out[s0:s0 + m] = torch.linalg.matrix_exp((1j * eps) * h)
+    return out.reshape(shape + (3, 3))
+
+
 def unit_links(dims) -> np.ndarray:
     """Free-field gauge configuration: every link is the 3x3 identity."""
     u = np.zeros(lattice_shape(dims) + (4, 3, 3), dtype=np.complex128)
