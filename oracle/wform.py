@@ -239,13 +239,19 @@ def _qmv(q, v):
     return np.concatenate([ou.reshape(shp + (2, 3)), ol.reshape(shp + (2, 3))], axis=-2)
 
 
+def apply_quads(quads_, psi, bc=(1, 1, 1, 1)):
+    """M psi by Eq. minFlopForm from the 27 precomputed quads (`quads(U, c)`), multiplying the 6x6
+    blocks directly (no 12x12 matrices)."""
+    out = np.zeros_like(psi, dtype=np.complex128)
+    for off, q in quads_.items():
+        out += _qmv(q, neighbour_spinor(psi, off, bc))
+    return out
+
+
 def apply_lean(U, c, psi, bc=(1, 1, 1, 1)):
     """M psi by Eq. minFlopForm, multiplying the 6x6 blocks directly (no 12x12 matrices), for
     lattices where the dense blocks would not fit in memory."""
-    out = np.zeros_like(psi, dtype=np.complex128)
-    for off, q in quads(U, c).items():
-        out += _qmv(q, neighbour_spinor(psi, off, bc))
-    return out
+    return apply_quads(quads(U, c), psi, bc)
 
 
 def _mv(W, v):
