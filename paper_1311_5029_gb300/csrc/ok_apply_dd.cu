@@ -56,46 +56,55 @@ __device__ __forceinline__ void prod_acc(float& s, float& t, dd a, dd b) {
 }
 __device__ __forceinline__ dd dneg(dd a) { return dd(-a.hi, -a.lo); }
 
-// y = V v (ADJ: V^dag v) for the matrix at wp (element e at wp + e * LANES).
-template <bool ADJ>
-__device__ __forceinline__ void matvec(const float4* __restrict__ wp, const cx<dd> (&v)[3], cx<dd> (&y)[3]) {
-  cx<dd> e[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) e[k] = ld4(wp + k * LANES);
+__device__ __forceinline__ dd dflip(dd a, unsigned m) {
+  return dd(__uint_as_float(__float_as_uint(a.hi) ^ m), __uint_as_float(__float_as_uint(a.lo) ^ m));
+}
+
+// y = V v, or V^dag v when adj, for the matrix at wp (element e at wp + e * LANES).  One body for
+// both forms: the adjoint reads element (c, r) for (r, c) and flips the sign of its imaginary
+// part; a row's three elements are loaded as the row starts.
+__device__ __forceinline__ void matvec(const float4* __restrict__ wp, bool adj, const cx<dd> (&v)[3], cx<dd> (&y)[3]) {
+  const int sr = adj ? 1 : 3, sc = adj ? 3 : 1;
+  const unsigned cj = adj ? 0x80000000u : 0u;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    float sr, tr, si, ti_;
+    cx<dd> e[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const cx<dd> a = ADJ ? e[3 * c + r] : e[3 * r + c];
-      // plain: (a.re v.re - a.im v.im) + i (a.re v.im + a.im v.re)
-      // adjoint (conj a): (a.re v.re + a.im v.im) + i (a.re v.im - a.im v.re)
-      const dd aim_re = ADJ ? a.im : dneg(a.im);
-      const dd aim_im = ADJ ? dneg(a.im) : a.im;
-      if (c == 0) {
-        prod_first(sr, tr, a.re, v[c].re);
-        prod_first(si, ti_, a.re, v[c].im);
-      } else {
-        prod_acc(sr, tr, a.re, v[c].re);
-        prod_acc(si, ti_, a.re, v[c].im);
-      }
-      prod_acc(sr, tr, aim_re, v[c].im);
-      prod_acc(si, ti_, aim_im, v[c].re);
+      e[c] = ld4(wp + (r * sr + c * sc) * LANES);
+      e[c].im = dflip(e[c].im, cj);
     }
-    y[r] = mk(dd_renorm(sr, tr), dd_renorm(si, ti_));
+    float sr_, tr, si, ti_;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      // (a.re v.re - a.im v.im) + i (a.re v.im + a.im v.re)
+      if (c == 0) {
+        prod_first(sr_, tr, e[c].re, v[c].re);
+        prod_first(si, ti_, e[c].re, v[c].im);
+      } else {
+        prod_acc(sr_, tr, e[c].re, v[c].re);
+        prod_acc(si, ti_, e[c].re, v[c].im);
+      }
+      prod_acc(sr_, tr, dneg(e[c].im), v[c].im);
+      prod_acc(si, ti_, e[c].im, v[c].re);
+    }
+    y[r] = mk(dd_renorm(sr_, tr), dd_renorm(si, ti_));
   }
 }
 
-__device__ __forceinline__ cx<dd> times_unit(cx<dd> y, int u) {
-  switch (u) {
-    case U_P1: return y;
-    case U_PI: return mk(dneg(y.im), y.re);
-    case U_M1: return mk(dneg(y.re), dneg(y.im));
-    case U_MI: return mk(y.im, dneg(y.re));
-    case U_1PI: return mk(y.re - y.im, y.re + y.im);
-    case U_1MI: return mk(y.re + y.im, y.im - y.re);
-    case U_M1MI: return mk(y.im - y.re, dneg(y.re + y.im));
-    default: return mk(dneg(y.re + y.im), y.re - y.im);  // -1 + i
+// w = unit x y for the units 1, i, -1, -i (codes 0..3: a quarter turn per step, exact) and
+// 1 + i, 1 - i, -1 - i, -1 + i (codes 4..7: g (1 + s i), s = -1 for odd codes, g = -1 from 6 on).
+__device__ __forceinline__ void times_unit(const cx<dd> (&y)[3], int u, cx<dd> (&w)[3]) {
+  if (u < 4) {
+    const bool sw = u & 1;
+    const unsigned mr = (((u + 1) >> 1) & 1) ? 0x80000000u : 0u, mi = ((u >> 1) & 1) ? 0x80000000u : 0u;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w[k] = mk(dflip(sw ? y[k].im : y[k].re, mr), dflip(sw ? y[k].re : y[k].im, mi));
+  } else {
+    const unsigned ms = (u & 1) ? 0x80000000u : 0u, mg = (u & 2) ? 0x80000000u : 0u;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      w[k] = mk(dflip(y[k].re - dflip(y[k].im, ms), mg), dflip(y[k].im + dflip(y[k].re, ms), mg));
   }
 }
 
@@ -127,17 +136,9 @@ __device__ __forceinline__ void prefetch_mat(const float4* wp) {
   for (int e = 0; e < 9; ++e) prefetch_l1(wp + e * LANES);
 }
 
-__device__ __forceinline__ void accumulate(cx<dd> (&acc)[3], const cx<dd> (&w)[3], int sc, dd f) {
+__device__ __forceinline__ void add_to(cx<dd> (&acc)[3], const cx<dd> (&w)[3]) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    if (sc == S1) {
-      acc[k].re = acc[k].re + w[k].re;
-      acc[k].im = acc[k].im + w[k].im;
-    } else {
-      acc[k].re = fma(f, w[k].re, acc[k].re);
-      acc[k].im = fma(f, w[k].im, acc[k].im);
-    }
-  }
+  for (int k = 0; k < 3; ++k) acc[k] = mk(acc[k].re + w[k].re, acc[k].im + w[k].im);
 }
 
 // ---------------------------------------------------------------------------- the kernel
@@ -238,22 +239,27 @@ __global__ void __launch_bounds__(DD_THREADS, OK_DD_MINB)
           const float4 f = slot[src * 3 + k][tid];
           v[k] = mk(dd(f.x, f.y), dd(f.z, f.w));
         }
-        if (A.flags & 2) matvec<true>(wp, v, y);
-        else matvec<false>(wp, v, y);
-#pragma unroll
+        matvec(wp, A.flags & 2, v, y);
+        // the one or two accumulators, each with its scalar and unit (a rolled loop: one copy of
+        // the code)
+#pragma unroll 1
         for (int j = 0; j < 2; ++j) {
-          const int d = A.dst[j];
-          if (d < 0) continue;
-          const int sc = A.mul[j] & 3, un = A.mul[j] >> 2;
+          const int d = j ? A.dst[1] : A.dst[0];
+          if (d < 0) break;
+          const int mul = j ? A.mul[1] : A.mul[0];
+          const int sc = mul & 3, un = mul >> 2;
           cx<dd> w[3];
+          times_unit(y, un, w);
+          if (sc != S1) {
+            const dd f = sc == SA ? a_ii : b_ii;
 #pragma unroll
-          for (int k = 0; k < 3; ++k) w[k] = times_unit(y[k], un);
-          const dd f = sc == SA ? a_ii : b_ii;
+            for (int k = 0; k < 3; ++k) w[k] = mk(f * w[k].re, f * w[k].im);
+          }
           switch (d) {
-            case 0: accumulate(acc0, w, sc, f); break;
-            case 1: accumulate(acc1, w, sc, f); break;
-            case 2: accumulate(acc2, w, sc, f); break;
-            default: accumulate(acc3, w, sc, f); break;
+            case 0: add_to(acc0, w); break;
+            case 1: add_to(acc1, w); break;
+            case 2: add_to(acc2, w); break;
+            default: add_to(acc3, w); break;
           }
         }
       }
