@@ -255,32 +255,51 @@ struct Lane {
   int g, t;            // groupID (lane >> 2), thread in group (lane & 3)
   bool wact;           // this lane holds W entries (output column g < 6, input colour t < 3)
   int off_f;           // forward: word offset of (Q[(s,c)][(0,t)], Q[(s,c)][(1,t)]) in a block
-  int off_b;           // adjoint: word offset of Q[(0,t)][(s,c)] (Q[(1,t)][(s,c)] two words on)
   int uh_f, uh_b;      // U_t / 2 entries [c][t] and [t][c]
   int s;               // output spin of this lane's column
-  int a_off;           // uint4 offset of this lane's A-fragment word in a site's FP16 record: t * 8 + g
+  int a_off;           // offset 4 g + t of this lane's A-fragment word in a projection's tile
+  int e_b;             // word offset of the adjoint entries' element 3 t + c in a block (4 words)
 };
 
-// FP16 input layout (the applied vectors, scaled): per (site, b) a tile of 3 colours x 8 pairs x
-// 2 units, unit (site, b, c, p, h) = (h_b spin 0, h_b spin 1) of right-hand side p + 8 h at colour c,
-// at 8-byte unit index ((site * 2 + b) * 3 + c) * 16 + 2 p + h (slots of absent right-hand sides
-// hold zeros).  Lane (g, t) finds both of its rows, right-hand sides g and g + 8, in one 16-byte
-// word: index ((site * 2 + b) * 3 + t) * 8 + g in uint4 units.
-constexpr int IN16_SITE_U4 = 48;   // uint4 per site (768 bytes)
-__host__ __device__ __forceinline__ size_t in16_index(int site, int b, int r, int c) {
-  return (((size_t)site * 2 + b) * 3 + c) * 16 + 2 * (r & 7) + (r >> 3);
+// FP16 input layout (the applied vectors, scaled): per (site, b) a 512-byte tile of 8 pairs x 4
+// colour slots x 16 bytes; the word of pair p and colour c < 3 holds right-hand side p in its
+// first 8 bytes and p + 8 in its last 8 (each: h_b spin 0, h_b spin 1).  Lane (g, t < 3) reads
+// word 4 g + t, both of its rows in one 16-byte load, so a quarter-warp reads 96 bytes of one
+// aligned 128-byte line (one L1 wavefront); the slots c = 3 (the zero K pairs) are never read,
+// and absent right-hand sides are zero.
+constexpr int IN16_TILE_U4 = 32;   // 16-byte words per (site, projection) tile
+__host__ __device__ __forceinline__ size_t in16_index(int site, int b, int r, int c) {  // 8-byte units
+  return ((((size_t)site * 2 + b) * IN16_TILE_U4) + 4 * (r & 7) + c) * 2 + (r >> 3);
 }
 
 // A fragments of the two projections of `site`.
 __device__ __forceinline__ void load_h(const uint4* __restrict__ f, int site, const Lane& L, AFrag& hp, AFrag& hm) {
+  const uint4* q = f + (size_t)site * (2 * IN16_TILE_U4) + L.a_off;
   uint4 u = make_uint4(0u, 0u, 0u, 0u), v = u;
   if (L.t < 3) {
-    const uint4* q = f + (size_t)site * IN16_SITE_U4 + L.a_off;
     u = __ldg(q);
-    v = __ldg(q + 24);
+    v = __ldg(q + IN16_TILE_U4);
   }
   hp.r[0] = u.x; hp.r[2] = u.y; hp.r[1] = u.z; hp.r[3] = u.w;
   hm.r[0] = v.x; hm.r[2] = v.y; hm.r[1] = v.z; hm.r[3] = v.w;
+}
+
+// Loads of W words that do not allocate in L1: every W byte is used once per application, so L1
+// is left to the neighbour tiles that several sites share.
+__device__ __forceinline__ uint2 ldw2(const unsigned* p) {
+  uint2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint4 ldw4(const unsigned* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned ldw1(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
 }
 
 // Power-of-two scale sigma of a system's FP16 apply inputs: sigma |r| < 2^10 for |r|^2 = rr;
@@ -297,53 +316,6 @@ __device__ __forceinline__ float solve_scale(double rr) {
 __device__ __forceinline__ unsigned pack_scaled(float re, float im, float sc) {
   const float a = fminf(fmaxf(re * sc, -65504.f), 65504.f), b = fminf(fmaxf(im * sc, -65504.f), 65504.f);
   return pack_h2(a, b);
-}
-
-// The 14 lattice shifts of a site's stencil, computed once per site by lanes 0..13 (lane k: shift
-// k), each packed as (site offset << 1) | (crosses an antiperiodic boundary an odd number of times):
-// k = 4 mu + {0: +1, 1: +2, 2: -1, 3: -2} for mu = x, y, z; 12: t + 1; 13: t - 1.
-__device__ __forceinline__ int shift_code(int lane, const int (&c)[4], const Geom& g) {
-  if (lane >= 14) return 0;
-  const int mu = lane < 12 ? lane >> 2 : 3;
-  const int j = lane < 12 ? lane & 3 : (lane == 12 ? 0 : 2);
-  const int d = j == 0 ? 1 : j == 1 ? 2 : j == 2 ? -1 : -2;
-  const int cm = mu == 0 ? c[0] : mu == 1 ? c[1] : mu == 2 ? c[2] : c[3];
-  const int Lm = g.L[mu], Sm = g.S[mu];
-  int x = cm + d, wraps = 0;
-  if (x >= Lm) { x -= Lm; ++wraps; if (x >= Lm) { x -= Lm; ++wraps; } }
-  if (x < 0) { x += Lm; ++wraps; if (x < 0) { x += Lm; ++wraps; } }
-  const int neg = ((g.bcneg >> mu) & 1) & wraps;
-  return ((x - cm) * Sm) * 2 | neg;
-}
-// Shift index of a displacement along mu (mu < 3: d in +-1, +-2; mu = 3: d = +-1).
-constexpr int shift_of(int mu, int d) {
-  return mu == 3 ? (d > 0 ? 12 : 13) : 4 * mu + (d == 1 ? 0 : d == 2 ? 1 : d == -1 ? 2 : 3);
-}
-
-struct Acc { float v[2][2][4]; };   // [output projection a][real, imaginary tile][c0..c3]
-
-__device__ __forceinline__ unsigned bsign(bool neg) { return neg ? 0x80008000u : 0u; }
-
-// Forward and backward halves of each hop type.  `rec` is the record of the site whose stored
-// matrices the hop uses (x for forward hops, the neighbour for backward ones).  `code` holds this
-// lane's shift code (shift_code); a hop's displacement is the sum of one or two shifts, read from
-// the lanes that computed them.
-struct Site {
-  int x;      // the site
-  int code;   // this lane's shift code
-};
-
-template <int MU, int DMU, int NU = -1, int DNU = 0>
-__device__ __forceinline__ int neighbour(const Site& S, unsigned& sm) {
-  const int a = __shfl_sync(0xffffffffu, S.code, shift_of(MU, DMU));
-  int off = a >> 1, neg = a & 1;
-  if constexpr (NU >= 0) {
-    const int b = __shfl_sync(0xffffffffu, S.code, shift_of(NU, DNU));
-    off += b >> 1;
-    neg ^= b & 1;
-  }
-  sm = neg ? 0x80008000u : 0u;
-  return S.x + off;
 }
 
 // The 27 hops of Eq. minFlopForm as a compile-time table.  Hop j has a displacement (mu, dmu)
@@ -391,7 +363,46 @@ __host__ __device__ constexpr HopDesc hop_desc(int j) {
   return HopDesc{I, -1, J, -sJ, {{LK_BWD, blk}, N0, N0}, {{0, 0, 0, 1}, {0, 1, 1, 0}, U0, U0}};
 }
 
-// What one hop has loaded: the neighbour's A fragments, up to three raw W words pairs, the sign.
+// Displacements of the 27 hops packed for a constant-memory table: 4 bits per coordinate (x, y, z,
+// t), two's complement.
+__host__ __device__ constexpr unsigned hop_disp(int j) {
+  const HopDesc d = hop_desc(j);
+  int v[4] = {0, 0, 0, 0};
+  if (d.mu >= 0) v[d.mu] += d.dmu;
+  if (d.nu >= 0) v[d.nu] += d.dnu;
+  return (unsigned)(v[0] & 15) | ((unsigned)(v[1] & 15) << 4) | ((unsigned)(v[2] & 15) << 8) | ((unsigned)(v[3] & 15) << 12);
+}
+struct HopDisp { unsigned d[32]; };
+__host__ __device__ constexpr HopDisp make_hop_disp() {
+  HopDisp t{};
+  for (int j = 0; j < 32; ++j) t.d[j] = j < NHOP ? hop_disp(j) : 0u;
+  return t;
+}
+__constant__ HopDisp k_hop_disp = make_hop_disp();
+
+// Neighbour code of hop `lane` (lanes 0..26, in parallel): (neighbour site << 1) | 1 when the hop
+// crosses an antiperiodic boundary an odd number of times.
+__device__ __forceinline__ int nbr_code(int lane, int x, const Geom& g) {
+  const unsigned w = k_hop_disp.d[lane & 31];
+  int r = x, idx = 0, neg = 0;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int L = g.L[mu];
+    const int cm = mu < 3 ? r % L : r;
+    if (mu < 3) r /= L;
+    const int d = ((int)(w << (28 - 4 * mu))) >> 28;   // sign-extended 4-bit field
+    int xm = cm + d, wraps = 0;
+    if (xm >= L) { xm -= L; ++wraps; if (xm >= L) { xm -= L; ++wraps; } }
+    if (xm < 0) { xm += L; ++wraps; if (xm < 0) { xm += L; ++wraps; } }
+    neg ^= ((g.bcneg >> mu) & 1) & wraps;
+    idx += xm * g.S[mu];
+  }
+  return (idx << 1) | neg;
+}
+
+struct Acc { float v[2][2][4]; };   // [output projection a][real, imaginary tile][c0..c3]
+
+// What one hop has loaded: the neighbour's A fragments, up to three raw W word pairs, the sign.
 struct HopRaw {
   AFrag hp, hm;
   unsigned w[3][2];
@@ -401,86 +412,86 @@ struct HopRaw {
 struct Ctx {
   const uint4* __restrict__ in;
   const unsigned* __restrict__ W;
-  Site S;
+  int x;      // the site
+  int code;   // this lane's neighbour code (nbr_code)
   Lane L;
 };
 
-template <int J>
+// AP: the lattice has an antiperiodic direction (else every boundary sign is +1).
+template <int J, bool AP>
 __device__ __forceinline__ void hop_load(const Ctx& C, HopRaw& R) {
   constexpr HopDesc d = hop_desc(J);
-  int n = C.S.x;
+  int n = C.x;
   R.sm = 0u;
-  if constexpr (d.mu >= 0) n = neighbour<d.mu, d.dmu, d.nu, d.dnu>(C.S, R.sm);
+  if constexpr (d.mu >= 0) {
+    const int code = __shfl_sync(0xffffffffu, C.code, J);
+    n = code >> 1;
+    if constexpr (AP) R.sm = (code & 1) ? 0x80008000u : 0u;
+  }
   load_h(C.in, n, C.L, R.hp, R.hm);
   constexpr bool at_nbr = d.ld[0].kind == LK_BWD;
-  const unsigned* rec = C.W + (size_t)(at_nbr ? n : C.S.x) * REC;
+  const unsigned* rec = C.W + (size_t)(at_nbr ? n : C.x) * REC;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     R.w[k][0] = R.w[k][1] = 0u;
     const int kind = d.ld[k].kind, blk = d.ld[k].blk;
     if (kind == LK_NONE || !C.L.wact) continue;
     if (kind == LK_FWD) {
-      const uint2 z = __ldg(reinterpret_cast<const uint2*>(rec + blk * BLKW + C.L.off_f));
+      const uint2 z = ldw2(rec + blk * BLKW + C.L.off_f);
       R.w[k][0] = z.x;
       R.w[k][1] = z.y;
     } else if (kind == LK_BWD) {
-      R.w[k][0] = __ldg(rec + blk * BLKW + C.L.off_b);
-      R.w[k][1] = __ldg(rec + blk * BLKW + C.L.off_b + 2);
+      // the four spin entries of element 3 t + c; this lane takes k = s and k = 2 + s
+      const uint4 z = ldw4(rec + blk * BLKW + C.L.e_b);
+      R.w[k][0] = C.L.s ? z.y : z.x;
+      R.w[k][1] = C.L.s ? z.w : z.z;
     } else {
-      const unsigned u = __ldg(rec + UHW + (kind == LK_UF ? C.L.uh_f : C.L.uh_b));
+      const unsigned u = ldw1(rec + UHW + (kind == LK_UF ? C.L.uh_f : C.L.uh_b));
       R.w[k][0] = C.L.s ? 0u : u;   // (U_t / 2) x 1 is diagonal in spin
       R.w[k][1] = C.L.s ? u : 0u;
     }
   }
 }
 
-template <int J>
+template <int J, bool AP>
 __device__ __forceinline__ void hop_compute(const HopRaw& R, Acc& A) {
   constexpr HopDesc d = hop_desc(J);
+  const unsigned sm0 = AP ? R.sm : 0u;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const UseDesc u = d.use[k];
     if (u.load < 0) continue;
     const int kind = d.ld[u.load].kind;
-    const unsigned sm = R.sm ^ (u.neg ? 0x80008000u : 0u);
+    const unsigned sm = sm0 ^ (u.neg ? 0x80008000u : 0u);
     const BFrag q = (kind == LK_FWD || kind == LK_UF) ? bf_fwd(R.w[u.load][0], R.w[u.load][1], sm)
                                                       : bf_bwd(R.w[u.load][0], R.w[u.load][1], sm);
     block_mma(A.v[u.out][0], A.v[u.out][1], u.in ? R.hm : R.hp, q);
   }
 }
 
-// Software pipeline over the hops of one site: the loads of hop j + TC_AHEAD are issued before the
-// products of hop j, so that TC_AHEAD + 1 hops' loads are in flight per warp.
-#ifndef TC_AHEAD
-#define TC_AHEAD 3
-#endif
-constexpr int TC_SLOTS = TC_AHEAD + 1;
-template <int J>
-__device__ __forceinline__ void pipe(const Ctx& C, HopRaw (&R)[TC_SLOTS], Acc& A) {
+// Software pipeline over the hop sequence, which runs on from one site of a warp into the next:
+// the loads of hop j + 2 are issued before the products of hop j (for j + 2 >= 27, hop j - 25 of the
+// warp's next site), so three hops' loads are in flight per warp and a site starts with its first
+// hops already loaded.  Three register slots divide the 27 hops, so a hop's slot is a constant.
+constexpr int TC_SLOTS = 3;
+static_assert(NHOP % TC_SLOTS == 0, "hop slots must divide the hop count");
+template <int J, bool AP>
+__device__ __forceinline__ void pipe(const Ctx& C, const Ctx& Cn, bool more, HopRaw (&R)[TC_SLOTS], Acc& A) {
   if constexpr (J < NHOP) {
-    if constexpr (J + TC_AHEAD < NHOP) hop_load<J + TC_AHEAD>(C, R[(J + TC_AHEAD) % TC_SLOTS]);
-    hop_compute<J>(R[J % TC_SLOTS], A);
-    pipe<J + 1>(C, R, A);
-  }
-}
-template <int J>
-__device__ __forceinline__ void prologue(const Ctx& C, HopRaw (&R)[TC_SLOTS]) {
-  if constexpr (J < TC_AHEAD) {
-    hop_load<J>(C, R[J % TC_SLOTS]);
-    prologue<J + 1>(C, R);
+    constexpr int JJ = J + TC_SLOTS - 1;
+    if constexpr (JJ < NHOP) hop_load<JJ, AP>(C, R[JJ % TC_SLOTS]);
+    else if (more) hop_load<JJ - NHOP, AP>(Cn, R[JJ % TC_SLOTS]);
+    hop_compute<J, AP>(R[J % TC_SLOTS], A);
+    pipe<J + 1, AP>(C, Cn, more, R, A);
   }
 }
 
-}  // namespace tc
-
-namespace tc {
-
-// The last block of a launch sums each live right-hand side's partials (in block order, with a
-// fixed tree) and finalises its state; every block first writes its per-right-hand-side sums.
-template <int NP, int THREADS>
+// The last block of a launch sums each live right-hand side's partials and finalises its state; the
+// right-hand sides are spread over the warps (warp w takes w, w + 4, ...), each summed by its warp's
+// lanes in a fixed order and a fixed shuffle tree.
+template <int NP>
 __device__ __forceinline__ void multi_finish(double (*bsum)[3], const bool* live, int nrhs, const TcEpi& ep) {
   __shared__ int last;
-  __shared__ double sh[NP][THREADS / 32];
   if (threadIdx.x < nrhs) {
 #pragma unroll
     for (int k = 0; k < NP; ++k) ep.part[(size_t)threadIdx.x * ep.pstride + (size_t)blockIdx.x * NP + k] = bsum[threadIdx.x][k];
@@ -492,43 +503,55 @@ __device__ __forceinline__ void multi_finish(double (*bsum)[3], const bool* live
   if (!last) return;
   __threadfence();
   const unsigned G = gridDim.x;
-  for (int r = 0; r < nrhs; ++r) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < nrhs; r += TC_WARPS) {
     if (!live[r]) continue;
+    const double* pr = ep.part + (size_t)r * ep.pstride;
     double w[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) w[k] = 0.0;
-    const double* pr = ep.part + (size_t)r * ep.pstride;
-    for (unsigned b0 = threadIdx.x; b0 < G; b0 += THREADS * 4) {
-      double tmp[4][NP];
+    for (unsigned b = lane; b < G; b += 32)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const unsigned b = b0 + u * THREADS;
+      for (int k = 0; k < NP; ++k) w[k] += __ldcg(pr + (size_t)b * NP + k);
 #pragma unroll
-        for (int k = 0; k < NP; ++k) tmp[u][k] = b < G ? __ldcg(pr + (size_t)b * NP + k) : 0.0;
-      }
+    for (int k = 0; k < NP; ++k)
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int k = 0; k < NP; ++k) w[k] += tmp[u][k];
-    }
-    block_sums<NP, THREADS>(w, sh);
-    if (threadIdx.x == 0) {
+      for (int o = 16; o > 0; o >>= 1) w[k] += __shfl_xor_sync(0xffffffffu, w[k], o);
+    if (lane == 0) {
       double tot[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
       for (int k = 0; k < NP; ++k) tot[k] = w[k];
       finalise(ep.st + r, ep.fin, tot);
     }
   }
+  __syncthreads();
   if (threadIdx.x == 0) *ep.ticket = 0u;
 }
 
-template <int EPI>
-__global__ void __launch_bounds__(TC_THREADS, 4) apply_tc_kernel(const unsigned* __restrict__ W, const uint4* __restrict__ in,
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+#ifndef OK_TC_MINB
+#define OK_TC_MINB 4
+#endif
+#ifndef OK_TC_PF
+#define OK_TC_PF 1
+#endif
+// Bulk prefetch of a site's W record (3216 bytes, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_rec(const unsigned* p) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "n"(REC * 4) : "memory");
+}
+
+template <int EPI, bool AP>
+__global__ void __launch_bounds__(TC_THREADS, OK_TC_MINB) apply_tc_kernel(const unsigned* __restrict__ W, const uint4* __restrict__ in,
                                                                  float4* __restrict__ out, Geom g, int nrhs, TcEpi ep) {
+  constexpr bool RED = EPI == EPI_DOT || EPI == EPI_TS;
   __shared__ bool live[MAX_RHS];
   __shared__ double bsum[MAX_RHS][3];
   __shared__ float wsum[TC_WARPS][MAX_RHS][3];
-  if (EPI != EPI_NONE) {
+  // the epilogue's operand units of the current site, copied in while its hops run
+  __shared__ __align__(16) float4 ybuf[RED ? TC_WARPS : 1][4][32];
+
+  if (RED) {
     if (threadIdx.x < MAX_RHS) live[threadIdx.x] = threadIdx.x < nrhs && ep.st[threadIdx.x].halt == HALT_NONE;
     __syncthreads();
     bool any = false;
@@ -543,10 +566,10 @@ __global__ void __launch_bounds__(TC_THREADS, 4) apply_tc_kernel(const unsigned*
   L.wact = L.g < 6 && L.t < 3;
   const int cc = L.g >> 1;
   L.off_f = 4 * (3 * cc + L.t) + 2 * L.s;
-  L.off_b = 4 * (3 * L.t + cc) + L.s;
   L.uh_f = 3 * cc + L.t;
   L.uh_b = 3 * L.t + cc;
-  L.a_off = 8 * L.t + L.g;
+  L.a_off = 4 * L.g + L.t;
+  L.e_b = 4 * (3 * L.t + cc);
   // 1 / sigma of the right-hand sides of this lane's rows (g and g + 8)
   float inv[2] = {1.f, 1.f};
 #pragma unroll
@@ -555,54 +578,85 @@ __global__ void __launch_bounds__(TC_THREADS, 4) apply_tc_kernel(const unsigned*
     if (r < nrhs) inv[h] = ep.inv_scale ? ep.inv_scale[r] : (ep.st ? 1.f / solve_scale(ep.st[r].rr) : 1.f);
   }
   float red[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};  // right-hand sides g and g + 8
-  const int nw = gridDim.x * TC_WARPS;
-  for (int x = blockIdx.x * TC_WARPS + warp; x < g.V; x += nw) {
-    int c[4];
-    {
-      int r = x;
-      c[0] = r % g.L[0]; r /= g.L[0];
-      c[1] = r % g.L[1]; r /= g.L[1];
-      c[2] = r % g.L[2]; c[3] = r / g.L[2];
-    }
-    const Ctx C{in, W, Site{x, shift_code(lane, c, g)}, L};
-    Acc A;
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int p = 0; p < 2; ++p)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) A.v[a][p][k] = 0.f;
+  // All warps sweep the lattice together, a band of gridDim.x * TC_WARPS consecutive sites at a time,
+  // so that a neighbour's tile is read again from L2 before it leaves.  With a grid of whole waves
+  // (k blocks on each of S multiprocessors, placed round robin) the k blocks of one multiprocessor
+  // take adjacent ranks, so its warps work on consecutive sites and share their x neighbours in L1.
+  const int G = gridDim.x, S = g.sms;
+  const int rank = (S > 0 && G % S == 0) ? (blockIdx.x % S) * (G / S) + blockIdx.x / S : blockIdx.x;
+  const int nw = G * TC_WARPS;
+  int x = rank * TC_WARPS + warp;
+  if (x < g.V) {
+    Ctx C{in, W, x, nbr_code(lane, x, g), L};
     HopRaw R[TC_SLOTS];
-    prologue<0>(C, R);
-    pipe<0>(C, R, A);
-    if (L.t < 3) {
+    hop_load<0, AP>(C, R[0]);
+    hop_load<1, AP>(C, R[1]);
+    for (;;) {
+      const int xn = x + nw;
+      const bool more = xn < g.V;
+      const Ctx Cn{in, W, more ? xn : x, more ? nbr_code(lane, xn, g) : C.code, L};
+      // the next site's own W record is read from DRAM once, block by block over its hops: have it
+      // in L2 before they start
+      if (OK_TC_PF && more && lane == 0) prefetch_rec(W + (size_t)xn * REC);
+      if constexpr (RED) {
+        // copy this site's epilogue operand units (FP32) into shared memory while the hops run
+        if (L.t < 3) {
 #pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const size_t row = ((size_t)x * 2 + a) * nrhs * 3;
+          for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int r = L.g + 8 * h;
-          if (r >= nrhs) continue;
-          const float f = inv[h];
-          const float4 o = make_float4(A.v[a][0][2 * h] * f, A.v[a][1][2 * h] * f, A.v[a][0][2 * h + 1] * f,
-                                       A.v[a][1][2 * h + 1] * f);
-          out[row + r * 3 + L.t] = o;
-          if (EPI == EPI_DOT || EPI == EPI_TS) {
-            const float4 y = __ldg(ep.y + row + r * 3 + L.t);
-            if (EPI == EPI_DOT) {  // conj(y) o
-              red[h][0] += y.x * o.x + y.y * o.y + y.z * o.z + y.w * o.w;
-              red[h][1] += y.x * o.y - y.y * o.x + y.z * o.w - y.w * o.z;
-            } else {               // conj(o) y, |o|^2
-              red[h][0] += o.x * y.x + o.y * y.y + o.z * y.z + o.w * y.w;
-              red[h][1] += o.x * y.y - o.y * y.x + o.z * y.w - o.w * y.z;
-              red[h][2] += o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
+            for (int h = 0; h < 2; ++h) {
+              const int r = L.g + 8 * h;
+              if (r < nrhs) {
+                const float4* src = ep.y + ((size_t)x * 2 + a) * nrhs * 3 + r * 3 + L.t;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(&ybuf[warp][2 * a + h][lane])),
+                             "l"(src)
+                             : "memory");
+              }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      }
+      Acc A;
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) A.v[a][p][k] = 0.f;
+      pipe<0, AP>(C, Cn, more, R, A);
+      if constexpr (RED) asm volatile("cp.async.wait_all;" ::: "memory");
+      if (L.t < 3) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const size_t row = ((size_t)x * 2 + a) * nrhs * 3;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = L.g + 8 * h;
+            if (r >= nrhs) continue;
+            const float f = inv[h];
+            const float4 o = make_float4(A.v[a][0][2 * h] * f, A.v[a][1][2 * h] * f, A.v[a][0][2 * h + 1] * f,
+                                         A.v[a][1][2 * h + 1] * f);
+            out[row + r * 3 + L.t] = o;
+            if constexpr (RED) {
+              const float4 y = ybuf[warp][2 * a + h][lane];
+              if (EPI == EPI_DOT) {  // conj(y) o
+                red[h][0] += y.x * o.x + y.y * o.y + y.z * o.z + y.w * o.w;
+                red[h][1] += y.x * o.y - y.y * o.x + y.z * o.w - y.w * o.z;
+              } else {               // conj(o) y, |o|^2
+                red[h][0] += o.x * y.x + o.y * y.y + o.z * y.z + o.w * y.w;
+                red[h][1] += o.x * y.y - o.y * y.x + o.z * y.w - o.w * y.z;
+                red[h][2] += o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
+              }
             }
           }
         }
       }
+      if (!more) break;
+      x = xn;
+      C = Cn;
     }
   }
-  if constexpr (EPI == EPI_DOT || EPI == EPI_TS) {
+  if constexpr (RED) {
     constexpr int NP = EPI == EPI_DOT ? 2 : 3;
     // lanes of one group (same g) hold the same right-hand sides: sum over t
 #pragma unroll
@@ -632,7 +686,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) apply_tc_kernel(const unsigned*
       }
     }
     __syncthreads();
-    multi_finish<NP, TC_THREADS>(bsum, live, nrhs, ep);
+    multi_finish<NP>(bsum, live, nrhs, ep);
   }
 }
 
@@ -700,6 +754,7 @@ __global__ void tc_to_canon_kernel(const float4* __restrict__ in, float2* __rest
 // threads: threadIdx.x = 3 r + c is one unit of a (site, projection) row, so every thread works on
 // one right-hand side r throughout and reads that system's scalars.  Rows are 2 V.
 constexpr int VEC_TARGET = 256;
+constexpr int TC_RED_CHUNK = 8;
 
 __device__ __forceinline__ void sys_scalars(const SolverState* st, int r, dcx& al, dcx& om, dcx& be, int& halt) {
   al = st[r].alpha;
@@ -819,7 +874,15 @@ __global__ void tc_update_xr_kernel(float4* __restrict__ x, const uint2* __restr
     const cx<float> om = mk<float>((float)st[r].omega.re, (float)st[r].omega.im);
     const float inv = 1.f / solve_scale(st[r].rr);
     const int L = 3 * nrhs;
-    for (long long row = blockIdx.x * (long long)blockDim.y + threadIdx.y; row < rows; row += (long long)gridDim.x * blockDim.y) {
+    // FP32 sums over a chunk of TC_RED_CHUNK rows, added into the FP64 totals once per chunk (FP64
+    // arithmetic runs at a small fraction of the FP32 rate)
+    const long long gs = (long long)gridDim.x * blockDim.y;
+    for (long long row0 = blockIdx.x * (long long)blockDim.y + threadIdx.y; row0 < rows; row0 += gs * TC_RED_CHUNK) {
+    float c3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < TC_RED_CHUNK; ++u) {
+      const long long row = row0 + u * gs;
+      if (row >= rows) break;
       const size_t i = (size_t)row * L + threadIdx.x;
       const float4 xv = x[i], sv = s[i], tv = t[i], hv = rhat[i];
       const size_t j = in16_index((int)(row >> 1), (int)(row & 1), r, threadIdx.x - 3 * r);
@@ -831,9 +894,13 @@ __global__ void tc_update_xr_kernel(float4* __restrict__ x, const uint2* __restr
       rv[i] = make_float4(r0.re, r0.im, r1.re, r1.im);
       cx<float> d = fma_cj(mk(hv.x, hv.y), r0, mk<float>(0.f, 0.f));
       d = fma_cj(mk(hv.z, hv.w), r1, d);
-      red[0] += d.re;
-      red[1] += d.im;
-      red[2] += (double)(r0.re * r0.re + r0.im * r0.im) + (double)(r1.re * r1.re + r1.im * r1.im);
+      c3[0] += d.re;
+      c3[1] += d.im;
+      c3[2] += (r0.re * r0.re + r0.im * r0.im) + (r1.re * r1.re + r1.im * r1.im);
+    }
+    red[0] += c3[0];
+    red[1] += c3[1];
+    red[2] += c3[2];
     }
   }
   vec_block_sums<3>(red, bsum, nrhs);
@@ -968,7 +1035,7 @@ int tc_blocks_needed(const ok_W* W) {
   static int resident = 0;
   if (resident == 0) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc::apply_tc_kernel<EPI_DOT>, tc::TC_THREADS, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc::apply_tc_kernel<EPI_DOT, false>, tc::TC_THREADS, 0) != cudaSuccess ||
         nb < 1)
       nb = 1;
     resident = nb * sm_count();
@@ -979,6 +1046,7 @@ int tc_blocks_needed(const ok_W* W) {
 
 int launch_apply_tc(const ok_W* W, const void* in16, cx<float>* out, int nrhs, int epi, const TcEpi& ep, cudaStream_t st) {
   if (!W || !W->Wtc || !in16 || !out || nrhs < 1 || nrhs > tc::MAX_RHS) return OK_EINVAL;
+  if (((uintptr_t)in16 | (uintptr_t)out) & 15) return OK_EINVAL;
   if (epi != EPI_NONE && epi != EPI_DOT && epi != EPI_TS) return OK_EINVAL;
   if (epi != EPI_NONE && (!ep.st || !ep.part || !ep.ticket || !ep.y)) return OK_EINVAL;
   const int grid = tc_blocks_needed(W);
@@ -988,19 +1056,24 @@ int launch_apply_tc(const ok_W* W, const void* in16, cx<float>* out, int nrhs, i
     TraceScope ts(names[epi], st);
     const uint4* i4 = (const uint4*)in16;
     float4* o4 = (float4*)out;
-    if (epi == EPI_NONE) tc::apply_tc_kernel<EPI_NONE><<<grid, tc::TC_THREADS, 0, st>>>(Wt, i4, o4, W->g, nrhs, ep);
-    else if (epi == EPI_DOT) tc::apply_tc_kernel<EPI_DOT><<<grid, tc::TC_THREADS, 0, st>>>(Wt, i4, o4, W->g, nrhs, ep);
-    else tc::apply_tc_kernel<EPI_TS><<<grid, tc::TC_THREADS, 0, st>>>(Wt, i4, o4, W->g, nrhs, ep);
+    Geom gs = W->g;
+    gs.sms = sm_count();
+    const bool ap = gs.bcneg != 0;
+#define OK_TC_LAUNCH(E, AP) tc::apply_tc_kernel<E, AP><<<grid, tc::TC_THREADS, 0, st>>>(Wt, i4, o4, gs, nrhs, ep)
+    if (epi == EPI_NONE) { if (ap) OK_TC_LAUNCH(EPI_NONE, true); else OK_TC_LAUNCH(EPI_NONE, false); }
+    else if (epi == EPI_DOT) { if (ap) OK_TC_LAUNCH(EPI_DOT, true); else OK_TC_LAUNCH(EPI_DOT, false); }
+    else { if (ap) OK_TC_LAUNCH(EPI_TS, true); else OK_TC_LAUNCH(EPI_TS, false); }
+#undef OK_TC_LAUNCH
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
 }
 
-size_t tc_in16_bytes(int V) { return (size_t)V * tc::IN16_SITE_U4 * 16; }
+size_t tc_in16_bytes(int V) { return (size_t)V * 2 * tc::IN16_TILE_U4 * 16; }
 
 int launch_to_tc16(const cx<float>* in, void* out16, int V, int nrhs, unsigned* amax, float* inv_scale, cudaStream_t st) {
   OK_CUDA_TRY(cudaMemsetAsync(amax, 0, sizeof(unsigned) * nrhs, st));
-  if (nrhs < tc::MAX_RHS) OK_CUDA_TRY(cudaMemsetAsync(out16, 0, tc_in16_bytes(V), st));  // absent right-hand sides
+  OK_CUDA_TRY(cudaMemsetAsync(out16, 0, tc_in16_bytes(V), st));  // absent right-hand sides
   const long long n4 = 6LL * V;  // float4 per right-hand side
   const int gx = grid_for(n4, 256) < 1024 ? grid_for(n4, 256) : 1024;
   {
