@@ -97,6 +97,12 @@ typedef struct {
 #define OK_SOLVE_MIXED  2  /* FP32 BiCGStab with FP64 reliable updates (needs both precisions) */
 #define OK_SOLVE_MIXED16 3 /* as OK_SOLVE_MIXED with the FP16 W copy in the FP32 iteration (OK_W_F16) */
 #define OK_SOLVE_MIXED_TC 4 /* ok_bicgstab_multi: as OK_SOLVE_MIXED with the tensor-core apply (OK_W_F16_TC) */
+/* Flag, or-ed into OK_SOLVE_MIXED, OK_SOLVE_MIXED16 or OK_SOLVE_MIXED_TC: outer FP64 defect correction.
+ * Each FP64 recomputation of r = b - M x (when the low-precision residual has dropped by delta)
+ * starts a fresh low-precision BiCGStab on the correction equation M e = r (rhat = p = r), whose
+ * increments accumulate into the FP64 x, instead of continuing the previous search direction
+ * (the reliable update).  info->reliable_updates counts the corrections. */
+#define OK_SOLVE_DEFECT 8
 
 typedef struct {
     double tol;          /* stop when |b - M x| / |b| < tol (true FP64 residual) */

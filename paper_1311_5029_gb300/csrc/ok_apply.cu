@@ -253,7 +253,7 @@ template <typename R, int EPI>
 __global__ void __launch_bounds__(APPLY_THREADS) apply_kernel(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi,
                                                               cx<R>* __restrict__ out, Geom g, R c0q, R a_ii, R b_ii,
                                                               EpiArgs<R> ep) {
-  if (EPI != EPI_NONE && ep.halt && *ep.halt) return;
+  if (ep.halt && *ep.halt) return;
   const int s = blockIdx.x * APPLY_THREADS + threadIdx.x;
   double red[3] = {0.0, 0.0, 0.0};
   if (s < g.V) {
@@ -369,7 +369,7 @@ template <typename R, int EPI>
 __global__ void __launch_bounds__(APPLY_THREADS, OK_APPLY_MINB) apply_pair_kernel(const cx<R>* __restrict__ W, const cx<R>* __restrict__ psi,
                                                                    cx<R>* __restrict__ out, Geom g, R c0q, R a_ii, R b_ii,
                                                                    EpiArgs<R> ep) {
-  if (EPI != EPI_NONE && ep.halt && *ep.halt) return;
+  if (ep.halt && *ep.halt) return;
   const int tid = blockIdx.x * APPLY_THREADS + threadIdx.x;
   const int s = tid >> 1;
   Pair pr;
@@ -629,7 +629,7 @@ template <typename R, int EPI, typename WT, bool STAGED>
 __global__ void __launch_bounds__(SPLIT_THREADS, EPI == EPI_NONE ? OK_SPLIT_MINB : OK_SPLIT_MINB_EPI) apply_split_kernel(const cx<WT>* __restrict__ W, const cx<R>* __restrict__ psi,
                                                                                    cx<R>* __restrict__ out, Geom g, R c0q, R a_ii, R b_ii,
                                                                                    EpiArgs<R> ep) {
-  if (EPI != EPI_NONE && ep.halt && *ep.halt) return;
+  if (ep.halt && *ep.halt) return;
   // Persistent: each block walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The hand-off buffer
   // is double-buffered by tile parity, so one barrier per tile suffices: the backward half writes
   // buffer k & 1 for tile k only after the barrier of tile k - 1, which the forward half passes

@@ -35,6 +35,18 @@ template <typename R> __device__ __forceinline__ cx<R> scal(dcx z) { return mk<R
 
 #define OK_GRID_STRIDE(i, n) for (long long i = blockIdx.x * (long long)BLAS_THREADS + threadIdx.x; i < (n); i += (long long)gridDim.x * BLAS_THREADS)
 
+// The reducing kernels sum RED_CHUNK units per thread in the vectors' own precision and add each
+// chunk's sums into the thread's FP64 totals: FP64 arithmetic runs at a small fraction of the FP32
+// rate on this part, so an FP64 conversion and add per unit would bound the kernel.  A chunk's
+// units (stride: the grid) are loaded together.  The order of every sum is fixed by the launch
+// shape, so results are reproducible.
+constexpr int RED_CHUNK = 8;
+#define OK_CHUNK_STRIDE(i0, n) \
+  for (long long i0 = blockIdx.x * (long long)BLAS_THREADS + threadIdx.x; i0 < (n); i0 += (long long)gridDim.x * BLAS_THREADS * RED_CHUNK)
+#define OK_CHUNK_UNITS(i, i0, n)                   \
+  _Pragma("unroll") for (int u_ = 0; u_ < RED_CHUNK; ++u_) \
+    if (const long long i = (i0) + (long long)u_ * gridDim.x * BLAS_THREADS; i < (n))
+
 // s = r - alpha v
 template <typename R>
 __global__ void __launch_bounds__(BLAS_THREADS) update_s_kernel(const typename Unit<R>::T* __restrict__ r,
@@ -77,25 +89,27 @@ __global__ void __launch_bounds__(BLAS_THREADS) update_xr_kernel(typename Unit<R
   using U = Unit<R>;
   const cx<R> al = scal<R>(st->alpha), om = scal<R>(st->omega);
   double red[3] = {0.0, 0.0, 0.0};
-  OK_GRID_STRIDE(i, nu) {
-    cx<R> xv[U::NC], pv[U::NC], sv[U::NC], tv[U::NC], hv[U::NC], zv[U::NC];
-    U::get(x[i], xv);
-    U::get(p[i], pv);
-    U::get(s[i], sv);
-    U::get(t[i], tv);
-    U::get(rhat[i], hv);
-    if (sx) U::get(sx[i], zv);
+  OK_CHUNK_STRIDE(i0, nu) {
     cx<R> d = mk<R>(0, 0);
     R n2 = 0;
+    OK_CHUNK_UNITS(i, i0, nu) {
+      cx<R> xv[U::NC], pv[U::NC], sv[U::NC], tv[U::NC], hv[U::NC], zv[U::NC];
+      U::get(x[i], xv);
+      U::get(p[i], pv);
+      U::get(s[i], sv);
+      U::get(t[i], tv);
+      U::get(rhat[i], hv);
+      if (sx) U::get(sx[i], zv);
 #pragma unroll
-    for (int k = 0; k < U::NC; ++k) {
-      xv[k] = xv[k] + al * pv[k] + om * (sx ? zv[k] : sv[k]);
-      sv[k] = sv[k] - om * tv[k];
-      d = fma_cj(hv[k], sv[k], d);
-      n2 += sv[k].re * sv[k].re + sv[k].im * sv[k].im;
+      for (int k = 0; k < U::NC; ++k) {
+        xv[k] = xv[k] + al * pv[k] + om * (sx ? zv[k] : sv[k]);
+        sv[k] = sv[k] - om * tv[k];
+        d = fma_cj(hv[k], sv[k], d);
+        n2 += sv[k].re * sv[k].re + sv[k].im * sv[k].im;
+      }
+      x[i] = U::put(xv);
+      r[i] = U::put(sv);
     }
-    x[i] = U::put(xv);
-    r[i] = U::put(sv);
     red[0] += d.re;
     red[1] += d.im;
     red[2] += n2;
@@ -125,6 +139,42 @@ __global__ void __launch_bounds__(BLAS_THREADS) update_p_kernel(typename Unit<R>
   }
 }
 
+// The inner products a BiCGStab half-iteration takes from its application of M, in a pass of their
+// own (the FP32 applications run without a fused epilogue; the separate pass over two vectors
+// costs less than the epilogue did): ALPHA: <a, b> (a = rhat, b = v) -> FIN_ALPHA;
+// OMEGA: <a, b>, <a, a> (a = t, b = s) -> FIN_OMEGA.
+template <typename R, bool OMEGA>
+__global__ void __launch_bounds__(BLAS_THREADS) dots_kernel(const typename Unit<R>::T* __restrict__ a,
+                                                            const typename Unit<R>::T* __restrict__ b, long long nu,
+                                                            SolverState* __restrict__ st, RedArgs ra, unsigned* ticket) {
+  if (st->halt) return;
+  using U = Unit<R>;
+  double red[3] = {0.0, 0.0, 0.0};
+  OK_CHUNK_STRIDE(i0, nu) {
+    cx<R> d = mk<R>(0, 0);
+    R n2 = 0;
+    OK_CHUNK_UNITS(i, i0, nu) {
+      cx<R> av[U::NC], bv[U::NC];
+      U::get(a[i], av);
+      U::get(b[i], bv);
+#pragma unroll
+      for (int k = 0; k < U::NC; ++k) {
+        d = fma_cj(av[k], bv[k], d);
+        if (OMEGA) n2 += av[k].re * av[k].re + av[k].im * av[k].im;
+      }
+    }
+    red[0] += d.re;
+    red[1] += d.im;
+    red[2] += n2;
+  }
+  if (OMEGA) {
+    grid_reduce<3, BLAS_THREADS>(red, ra, ticket);
+  } else {
+    double v2[2] = {red[0], red[1]};
+    grid_reduce<2, BLAS_THREADS>(v2, ra, ticket);
+  }
+}
+
 // Restart: rhat = p = r (same precision), sum <r, r> -> FIN_RESTART.
 template <typename R>
 __global__ void __launch_bounds__(BLAS_THREADS) restart_kernel(const typename Unit<R>::T* __restrict__ r,
@@ -133,14 +183,18 @@ __global__ void __launch_bounds__(BLAS_THREADS) restart_kernel(const typename Un
                                                                SolverState* __restrict__ st, RedArgs ra) {
   using U = Unit<R>;
   double red[1] = {0.0};
-  OK_GRID_STRIDE(i, nu) {
-    typename U::T u = r[i];
-    rhat[i] = u;
-    p[i] = u;
-    cx<R> a[U::NC];
-    U::get(u, a);
+  OK_CHUNK_STRIDE(i0, nu) {
+    R n2 = 0;
+    OK_CHUNK_UNITS(i, i0, nu) {
+      typename U::T u = r[i];
+      rhat[i] = u;
+      p[i] = u;
+      cx<R> a[U::NC];
+      U::get(u, a);
 #pragma unroll
-    for (int k = 0; k < U::NC; ++k) red[0] += (double)a[k].re * a[k].re + (double)a[k].im * a[k].im;
+      for (int k = 0; k < U::NC; ++k) n2 += a[k].re * a[k].re + a[k].im * a[k].im;
+    }
+    red[0] += n2;
   }
   grid_reduce<1, BLAS_THREADS>(red, ra, &st->ticket[3]);
 }
@@ -152,20 +206,26 @@ __global__ void __launch_bounds__(BLAS_THREADS) demote_kernel(const double2* __r
                                                               float2* __restrict__ rhat, float2* __restrict__ p,
                                                               long long n, SolverState* __restrict__ st, RedArgs ra) {
   double red[3] = {0.0, 0.0, 0.0};
-  OK_GRID_STRIDE(i, n) {
-    double2 d = r64[i];
-    float2 f = make_float2((float)d.x, (float)d.y);
-    r32[i] = f;
-    if (RESTART) {
-      rhat[i] = f;
-      p[i] = f;
-      red[0] += (double)f.x * f.x + (double)f.y * f.y;
-    } else {
-      float2 h = rhat[i];
-      red[0] += (double)h.x * f.x + (double)h.y * f.y;
-      red[1] += (double)h.x * f.y - (double)h.y * f.x;
-      red[2] += (double)f.x * f.x + (double)f.y * f.y;
+  OK_CHUNK_STRIDE(i0, n) {
+    float c[3] = {0.f, 0.f, 0.f};
+    OK_CHUNK_UNITS(i, i0, n) {
+      double2 d = r64[i];
+      float2 f = make_float2((float)d.x, (float)d.y);
+      r32[i] = f;
+      if (RESTART) {
+        rhat[i] = f;
+        p[i] = f;
+        c[0] += f.x * f.x + f.y * f.y;
+      } else {
+        float2 h = rhat[i];
+        c[0] += h.x * f.x + h.y * f.y;
+        c[1] += h.x * f.y - h.y * f.x;
+        c[2] += f.x * f.x + f.y * f.y;
+      }
     }
+    red[0] += c[0];
+    red[1] += c[1];
+    red[2] += c[2];
   }
   if (RESTART) {
     double v1[1] = {red[0]};
@@ -232,8 +292,14 @@ int blas_blocks(long long units) {
 // (from the occupancy calculator; a grid-stride loop covers the rest).  A wider grid would leave a
 // partial second wave that every thread of the first must wait for: the kernels that hold more
 // registers (update_xr at 48) fit 5 blocks of 256 threads per SM, not 8.
+// Kernels that end in a grid reduction take at most this many blocks per multiprocessor: every
+// block's partial ends in a fence and an atomic on one completion counter, and at a full wave
+// (up to 8 x 152 blocks) those serialised atomics cost more than the few extra loads in flight.
+#ifndef OK_RED_BLOCKS_PER_SM
+#define OK_RED_BLOCKS_PER_SM 2
+#endif
 template <typename K>
-static int wave_blocks(K kern, long long units) {
+static int wave_blocks(K kern, long long units, bool reduces = false) {
   static std::mutex mu;
   static std::vector<std::pair<const void*, int>> cache;
   int per_sm = 0;
@@ -248,6 +314,7 @@ static int wave_blocks(K kern, long long units) {
       cache.emplace_back((const void*)kern, per_sm);
     }
   }
+  if (reduces && per_sm > OK_RED_BLOCKS_PER_SM) per_sm = OK_RED_BLOCKS_PER_SM;
   const long long need = (units + BLAS_THREADS - 1) / BLAS_THREADS;
   const long long cap = (long long)sm_count() * per_sm;
   return (int)(need < cap ? (need > 0 ? need : 1) : cap);
@@ -275,8 +342,26 @@ int launch_update_xr(cx<R>* x, const cx<R>* p, const cx<R>* s, const cx<R>* t, c
   RedArgs ra{st, part, nullptr, FIN_XR};
   {
     TraceScope ts(sizeof(R) == 8 ? "update_xr_f64" : "update_xr_f32", strm);
-    update_xr_kernel<R><<<wave_blocks(update_xr_kernel<R>, nu), BLAS_THREADS, 0, strm>>>((T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r,
+    update_xr_kernel<R><<<wave_blocks(update_xr_kernel<R>, nu, true), BLAS_THREADS, 0, strm>>>((T*)x, (const T*)p, (const T*)s, (const T*)t, (T*)r,
                                                                   (const T*)rhat, nu, st, ra, 0, (const T*)sx);
+  }
+  OK_LAUNCH_CHECK();
+  return OK_SUCCESS;
+}
+
+template <typename R>
+int launch_dots(const cx<R>* a, const cx<R>* b, long long n, bool omega, SolverState* st, double* part, cudaStream_t strm) {
+  using T = typename Unit<R>::T;
+  long long nu = units_of<R>(n);
+  RedArgs ra{st, part, nullptr, omega ? FIN_OMEGA : FIN_ALPHA};
+  {
+    TraceScope ts(omega ? (sizeof(R) == 8 ? "dots_ts_f64" : "dots_ts_f32") : (sizeof(R) == 8 ? "dot_rv_f64" : "dot_rv_f32"), strm);
+    if (omega)
+      dots_kernel<R, true><<<wave_blocks(dots_kernel<R, true>, nu, true), BLAS_THREADS, 0, strm>>>((const T*)a, (const T*)b, nu, st, ra,
+                                                                                          &st->ticket[omega ? 1 : 0]);
+    else
+      dots_kernel<R, false><<<wave_blocks(dots_kernel<R, false>, nu, true), BLAS_THREADS, 0, strm>>>((const T*)a, (const T*)b, nu, st, ra,
+                                                                                            &st->ticket[0]);
   }
   OK_LAUNCH_CHECK();
   return OK_SUCCESS;
@@ -400,6 +485,8 @@ int launch_norms(const cx<double>* x, const cx<double>* b, long long n, SolverSt
 
 template int launch_update_s<double>(const cx<double>*, const cx<double>*, cx<double>*, long long, const SolverState*, cudaStream_t);
 template int launch_update_s<float>(const cx<float>*, const cx<float>*, cx<float>*, long long, const SolverState*, cudaStream_t);
+template int launch_dots<float>(const cx<float>*, const cx<float>*, long long, bool, SolverState*, double*, cudaStream_t);
+template int launch_dots<double>(const cx<double>*, const cx<double>*, long long, bool, SolverState*, double*, cudaStream_t);
 template int launch_update_xr<double>(cx<double>*, const cx<double>*, const cx<double>*, const cx<double>*, cx<double>*, const cx<double>*, long long, SolverState*, double*, cudaStream_t, const cx<double>*);
 template int launch_update_xr<float>(cx<float>*, const cx<float>*, const cx<float>*, const cx<float>*, cx<float>*, const cx<float>*, long long, SolverState*, double*, cudaStream_t, const cx<float>*);
 template int launch_update_p<double>(cx<double>*, const cx<double>*, const cx<double>*, long long, const SolverState*, cudaStream_t);

@@ -66,7 +66,7 @@ int tc_vec_blocks(int nrhs);
 int launch_apply_tc(const ok_W* W, const void* in16, cx<float>* out, int nrhs, int epi, const TcEpi& ep, cudaStream_t st);
 // canonical complex64 [nrhs][V][4][3] -> FP16 tensor-core layout with a power-of-two scale per right-hand
 // side (amax: nrhs words of scratch; inv_scale: nrhs floats out, 1 / sigma); FP32 tensor-core layout -> canonical.
-size_t tc_in16_bytes(int V);  // the FP16 input layout of the tensor-core apply (768 bytes per site)
+size_t tc_in16_bytes(int V);  // the FP16 input layout of the tensor-core apply (1 KB per site)
 int launch_to_tc16(const cx<float>* in, void* out16, int V, int nrhs, unsigned* amax, float* inv_scale, cudaStream_t st);
 int launch_from_tc(const cx<float>* in, cx<float>* out, int V, int nrhs, cudaStream_t st);
 int launch_tc_update_s(const cx<float>* r, const cx<float>* v, cx<float>* s, void* s16, int V, int nrhs, const SolverState* st,
@@ -92,6 +92,9 @@ int launch_update_xr(cx<R>* x, const cx<R>* p, const cx<R>* s, const cx<R>* t, c
                      SolverState* st, double* part, cudaStream_t strm, const cx<R>* sx = nullptr);
 template <typename R>
 int launch_update_p(cx<R>* p, const cx<R>* r, const cx<R>* v, long long n, const SolverState* st, cudaStream_t strm);
+// <a, b> -> FIN_ALPHA (a = rhat, b = v), or with omega <a, b>, <a, a> -> FIN_OMEGA (a = t, b = s).
+template <typename R>
+int launch_dots(const cx<R>* a, const cx<R>* b, long long n, bool omega, SolverState* st, double* part, cudaStream_t strm);
 template <typename R>
 int launch_restart(const cx<R>* r, cx<R>* rhat, cx<R>* p, long long n, SolverState* st, double* part, cudaStream_t strm);
 int launch_demote(const cx<double>* r64, cx<float>* r32, cx<float>* rhat, cx<float>* p, long long n, bool restart,

@@ -124,8 +124,12 @@ int iterate(const ok_W* W, const IterBufs<R>& b, long long n, SolverState* dst, 
       pin = pc.zp;
     }
   }
+  // FP32: plain applications, their inner products in separate passes (cheaper than the fused
+  // epilogue in this kernel); FP64: the epilogue is fused (the FP64 pipe bounds that kernel).
+  constexpr bool fused = sizeof(R) == 8;
   EpiArgs<R> e1{b.rhat, nullptr, RedArgs{dst, part, nullptr, FIN_ALPHA}, &dst->ticket[0], &dst->halt};
-  OK_TRY(apply_iter<R>(W, pin, b.v, EPI_DOT, e1, w16, st));
+  OK_TRY(apply_iter<R>(W, pin, b.v, fused ? EPI_DOT : EPI_NONE, e1, w16, st));
+  if (!fused) OK_TRY(launch_dots<R>(b.rhat, b.v, n, false, dst, part, st));
   OK_TRY(launch_update_s<R>(b.r, b.v, b.s, n, dst, st));
   if constexpr (sizeof(R) == 4) {
     if (pre) {
@@ -134,7 +138,8 @@ int iterate(const ok_W* W, const IterBufs<R>& b, long long n, SolverState* dst, 
     }
   }
   EpiArgs<R> e2{pre ? b.s : nullptr, nullptr, RedArgs{dst, part, nullptr, FIN_OMEGA}, &dst->ticket[1], &dst->halt};
-  OK_TRY(apply_iter<R>(W, sin, b.t, EPI_TS, e2, w16, st));
+  OK_TRY(apply_iter<R>(W, sin, b.t, fused ? EPI_TS : EPI_NONE, e2, w16, st));
+  if (!fused) OK_TRY(launch_dots<R>(b.t, b.s, n, true, dst, part, st));
   OK_TRY(launch_update_xr<R>(b.x, pin, b.s, b.t, b.r, b.rhat, n, dst, part, st, pre ? sin : nullptr));
   OK_TRY(launch_update_p<R>(b.p, b.r, b.v, n, dst, st));
   return OK_SUCCESS;
@@ -166,10 +171,12 @@ int bicgstab_impl(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok
   auto t0 = std::chrono::steady_clock::now();
   if (!W || !bvec || !x || !prm) return OK_EINVAL;
   if (!(prm->tol > 0.0) || prm->maxiter < 1 || prm->max_restarts < 0 || prm->check_every < 1) return OK_EINVAL;
-  int mode = prm->mode;
+  int mode = prm->mode & ~OK_SOLVE_DEFECT;
+  const bool defect = (prm->mode & OK_SOLVE_DEFECT) != 0;  // outer defect correction (restart at each update)
   const bool has64 = W->W64 || W->Wdf;  // an FP64-accurate copy for the true residual
   if (mode == OK_SOLVE_AUTO) mode = (W->W32 && has64) ? OK_SOLVE_MIXED : OK_SOLVE_F64;
   if (mode != OK_SOLVE_F64 && mode != OK_SOLVE_MIXED && mode != OK_SOLVE_MIXED16) return OK_EINVAL;
+  if (defect && mode == OK_SOLVE_F64) return OK_EINVAL;  // defect correction needs a low-precision iteration
   const bool w16 = mode == OK_SOLVE_MIXED16;
   if (w16) {
     if (!W->W16) return OK_EINVAL;
@@ -301,10 +308,15 @@ int bicgstab_impl(const ok_W* W, const cx<double>* bvec, cx<double>* x, const ok
     if (rr_true < h->tol2 * h->bb) return finish(OK_SUCCESS, rr_true);
     if (halt == HALT_MAXITER || h->iter >= prm->maxiter) return finish(OK_ENOCONV, rr_true);
     if (mode == OK_SOLVE_MIXED && halt == HALT_UPDATE) {
-      // reliable update: continue from the FP64 residual with the same search direction
       inf.reliable_updates++;
-      OK_TRY(launch_demote(r64, b32.r, b32.rhat, b32.p, n, false, dst, part, st));
-      OK_TRY(launch_update_p<float>(b32.p, b32.r, b32.v, n, dst, st));
+      if (defect) {
+        // outer defect correction: a fresh inner BiCGStab on M e = r from the FP64 residual
+        OK_TRY(launch_demote(r64, b32.r, b32.rhat, b32.p, n, true, dst, part, st));
+      } else {
+        // reliable update: continue from the FP64 residual with the same search direction
+        OK_TRY(launch_demote(r64, b32.r, b32.rhat, b32.p, n, false, dst, part, st));
+        OK_TRY(launch_update_p<float>(b32.p, b32.r, b32.v, n, dst, st));
+      }
       OK_TRY(enqueue(prm->check_every));
       continue;
     }
@@ -400,7 +412,8 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
   if (!W || !bvec || !x || !prm || nrhs < 1 || nrhs > 64) return OK_EINVAL;
   if (!(prm->tol > 0.0) || prm->maxiter < 1 || prm->max_restarts < 0 || prm->check_every < 1) return OK_EINVAL;
   if (!(prm->delta > 0.0 && prm->delta < 1.0)) return OK_EINVAL;
-  int mode = prm->mode;
+  int mode = prm->mode & ~OK_SOLVE_DEFECT;
+  const bool defect = (prm->mode & OK_SOLVE_DEFECT) != 0;  // outer defect correction (restart at each update)
   if (mode == OK_SOLVE_AUTO)
     mode = (W->Wtc && nrhs <= 16 && !net) ? OK_SOLVE_MIXED_TC : W->W16 ? OK_SOLVE_MIXED16 : OK_SOLVE_MIXED;
   if (mode != OK_SOLVE_MIXED && mode != OK_SOLVE_MIXED16 && mode != OK_SOLVE_MIXED_TC) return OK_EINVAL;
@@ -459,12 +472,13 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
   SolverState* dst = ws.get<SolverState>(nrhs, &err);
   unsigned* tickets = tcp ? ws.get<unsigned>(4, &err) : nullptr;  // grid completion counters of the TC kernels
   // FP16 copies of p and s (scaled per system) that the tensor-core apply reads
-  unsigned char* p16 = tcp ? ws.get<unsigned char>(tc_in16_bytes(W->g.V), &err) : nullptr;
-  unsigned char* s16 = tcp ? ws.get<unsigned char>(tc_in16_bytes(W->g.V), &err) : nullptr;
+  const size_t b16 = tcp ? tc_in16_bytes(W->g.V) : 0;
+  unsigned char* p16 = tcp ? ws.get<unsigned char>(b16, &err) : nullptr;
+  unsigned char* s16 = tcp ? ws.get<unsigned char>(b16, &err) : nullptr;
   if (tcp && (!tickets || !p16 || !s16)) { set_cuda_error(err); return OK_ENOMEM; }
-  if (tcp) {  // the slots of absent right-hand sides stay zero
-    OK_CUDA_TRY(cudaMemsetAsync(p16, 0, tc_in16_bytes(W->g.V), st));
-    OK_CUDA_TRY(cudaMemsetAsync(s16, 0, tc_in16_bytes(W->g.V), st));
+  if (tcp) {  // absent right-hand sides stay zero; a halted system's copies stay finite
+    OK_CUDA_TRY(cudaMemsetAsync(p16, 0, b16, st));
+    OK_CUDA_TRY(cudaMemsetAsync(s16, 0, b16, st));
   }
   if (tcp) OK_CUDA_TRY(cudaMemsetAsync(tickets, 0, 4 * sizeof(unsigned), st));
   const int V = W->g.V;
@@ -621,7 +635,14 @@ int bicgstab_multi(const ok_W* W, int nrhs, const cx<double>* bvec, cx<double>* 
       if (halt == HALT_MAXITER || h[k].iter >= prm->maxiter) { status[k] = OK_ENOCONV; OK_CUDA_TRY(freeze(k)); continue; }
       if (halt == HALT_UPDATE) {
         inf[k].reliable_updates++;
-        if (tcp) {
+        if (defect) {  // outer defect correction: a fresh inner BiCGStab from the FP64 residual
+          if (tcp) {
+            OK_TRY(launch_tc_demote(r64, b.r, b.rhat, b.p, V, nrhs, k, true, &dst[k], part, st));
+            OK_TRY(launch_tc_half(b.p, p16, V, nrhs, dst, k, st));
+          } else {
+            OK_TRY(launch_demote(r64, vec(b.r, k), vec(b.rhat, k), vec(b.p, k), n, true, &dst[k], part, st));
+          }
+        } else if (tcp) {
           OK_TRY(launch_tc_demote(r64, b.r, b.rhat, b.p, V, nrhs, k, false, &dst[k], part, st));
           OK_TRY(launch_tc_update_p(b.p, p16, b.r, b.v, V, nrhs, dst, k, st));
         } else {

@@ -134,3 +134,20 @@ def test_mixed_solve_with_double_float_residuals():
     assert oracle_relres(U, c, b, x.cpu().numpy(), bc, lean=True) < TOL
     with pytest.raises(ok.OKError):   # plain FP64 iteration needs the native copy
         ok.bicgstab(W, to_dev(b), tol=TOL, mode=ok.SOLVE_F64)
+
+
+@pytest.mark.parametrize("base", ["mixed", "mixed16"])
+def test_16cube32_outer_defect_correction(base):
+    """The 16^3 x 32 workload with the outer FP64 defect correction (OK_SOLVE_DEFECT): every
+    correction restarts the low-precision BiCGStab (FP32 or FP16 W, FP32 fields) on M e = r, and
+    the FP64 solution reaches a true residual below 1e-10 checked with the oracle's apply."""
+    dims, U, c, b = synth.workload_inputs("16^3x32")
+    bc = (1, 1, 1, 1)
+    W = ok.precompute_W(to_dev(U), c, bc, ok.W_DF64 | ok.W_F32 | ok.W_F16)
+    m = (ok.SOLVE_MIXED if base == "mixed" else ok.SOLVE_MIXED16) | ok.SOLVE_DEFECT
+    x, info = ok.bicgstab(W, to_dev(b), tol=TOL, mode=m, delta=1e-3)
+    r = oracle_relres(U, c, b, x.cpu().numpy(), bc, lean=True)
+    assert info["status"] == 0 and r < TOL and info["true_relres"] < TOL, (info, r)
+    assert info["reliable_updates"] >= 2
+    with pytest.raises(ok.OKError):  # plain FP64 has no low-precision inner solve to correct
+        ok.bicgstab(W, to_dev(b), tol=TOL, mode=ok.SOLVE_F64 | ok.SOLVE_DEFECT)

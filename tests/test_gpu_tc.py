@@ -110,6 +110,21 @@ def test_tc_apply_full_size_20cube64_sampled():
         assert rel_l2(gk, exp) < TC_TOL and rel_max(gk, exp) < TC_TOL, (k, rel_l2(gk, exp))
 
 
+def test_tc_solve_outer_defect_correction():
+    """The tensor-core iteration as the inner solve of an outer FP64 defect correction
+    (OK_SOLVE_MIXED_TC | OK_SOLVE_DEFECT): every system to a true residual below 1e-10."""
+    dims, bc = (6, 5, 4, 8), (1, 1, 1, -1)
+    U = synth.random_links(dims, 0.3, 9551)
+    c = synth.placeholder_coeffs(0.6)
+    W = ok.precompute_W(to_dev(U), c, bc, ok.W_DF64 | ok.W_F16_TC)
+    b = spin_colour_sources(dims, site=9)
+    x, infos = ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED_TC | ok.SOLVE_DEFECT, delta=1e-3, check_every=4)
+    xs, bs = x.cpu().numpy(), b.cpu().numpy()
+    for k in range(12):
+        r = np.linalg.norm(bs[k] - wform.apply(U, c, xs[k], bc)) / np.linalg.norm(bs[k])
+        assert infos[k]["true_relres"] < 1e-10 and r < 1e-10 and infos[k]["reliable_updates"] >= 2, (k, infos[k], r)
+
+
 @pytest.mark.parametrize("w64", ["f64", "df64"])
 def test_tc_solve_spin_colour_sources_small(w64):
     dims, bc = (6, 5, 4, 8), (1, 1, 1, -1)
@@ -161,8 +176,8 @@ def test_tc_argument_errors():
         ok.apply_M_multi(W2, many, prec=ok.F16_TC)
 
 
-@pytest.mark.parametrize("am0", [0.3, 1.0, 2.5])
-def test_tc_solve_20cube64_twelve_sources(am0):
+@pytest.mark.parametrize("am0,defect", [(0.3, False), (1.0, False), (2.5, False), (1.0, True)])
+def test_tc_solve_20cube64_twelve_sources(am0, defect):
     """The 20^3 x 64 workload: the 12 spin-colour point sources in one lockstep solve on the tensor
     cores (FP16 operands, FP32 accumulation and vectors, FP64 reliable updates), graph-captured;
     every system to a true FP64 residual below 1e-10 (the GPU residual for all twelve, the
@@ -173,7 +188,8 @@ def test_tc_solve_20cube64_twelve_sources(am0):
     c = synth.placeholder_coeffs(am0)
     W = ok.precompute_W(to_dev(U), c, (1, 1, 1, 1), ok.W_F64 | ok.W_F16_TC)
     b = spin_colour_sources(dims)
-    x, infos = ok.bicgstab_multi(W, b, tol=1e-10, mode=ok.SOLVE_MIXED_TC, delta=1e-4, check_every=8)
+    mode = ok.SOLVE_MIXED_TC | (ok.SOLVE_DEFECT if defect else 0)
+    x, infos = ok.bicgstab_multi(W, b, tol=1e-10, mode=mode, delta=1e-4, check_every=8)
     for k in range(12):
         assert infos[k]["true_relres"] < 1e-10, (k, infos[k])
         assert ok.true_residual(W, b[k].contiguous(), x[k].contiguous()) < 1e-10
