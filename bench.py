@@ -7,14 +7,22 @@ am0 0.5, Gaussian source), with inputs resident in HBM:
   double-float copy and an FP32 copy), BiCGStab solve of M x = b to a true FP64 residual
   |b - M x| / |b| < 1e-10 (FP32 iteration with reliable updates whose FP64-accurate residuals run
   in double-float arithmetic on the FP32 pipes), release of W.
-`value` is the step's algorithmic HBM traffic (bytes each kernel must move once) divided by the
-step time, in GB/s.  `roofline` describes the dominant kernel (the FP32 application of M inside
-the solve) timed with CUDA events on its own stream during the timed steps.  `e2e` repeats the
-step through the public API with the links and the source copied from pinned host memory and the
-solution copied back inside the timed region.
+`value` is the step's algorithmic HBM traffic (each byte a kernel must move, counted once; the
+FP64-accurate work at FP64 bytes whatever its representation) divided by the step time, in GB/s:
+a throughput of the whole step, not of the apply alone.  `roofline` describes the dominant kernel
+(the FP32 application of M inside the solve, the metric's M.psi GB/s) timed with CUDA events on
+its own stream during the timed steps.  `e2e` repeats the step through the public API with the
+links and the source copied from pinned host memory and the solution copied back inside the timed
+region.
+
+Two further keys time the solve forms the metric compares with plain FP64 BiCGStab, outside the
+timed steps: `multi_rhs` (20^3 x 64, the 12 spin-colour point sources of one propagator in one
+lockstep solve on the tensor cores) and `large` (28^3 x 96, the same at 2.1 M sites, with the device
+memory in use); each against plain FP64 BiCGStab timed on two of the sources and scaled to twelve.
 
 --impl reference times the oracle (plain FP64 numpy CPU code) on the same workload and metric: each
-step is one oracle application of M on the full lattice (a bounded sample of the solve).
+step is one oracle application of M on the full lattice, its W evaluated once beforehand.
+--oracle-solve times the oracle's BiCGStab on the 16^3 x 32 workload once (minutes of CPU).
 
 Multi-GPU: one process per GPU under torch.distributed; each rank solves its own replica (its own
 source), so the work per GPU is fixed ("scaling": "weak") and no data moves between ranks.
@@ -42,20 +50,19 @@ TOL = 1e-10
 DELTA = 1e-4        # reliable-update threshold of the mixed solver (tuned on this workload)
 CHECK_EVERY = 4
 
-# Algorithmic bytes per site (each stored byte read once, each output written once).
+# Algorithmic bytes per site (each stored byte read once, each output written once).  FP64-accurate
+# work is charged at FP64 bytes whatever representation carries it (the double-float copy holds
+# each FP64 number as two floats; that is an implementation choice, not algorithmic traffic).
 W64_BYTES = 43 * 9 * 16          # stored FP64 W per site
-WDF_BYTES = 43 * 9 * 32          # stored double-float W per site (two floats per FP64 component)
 W32_BYTES = 43 * 9 * 8           # stored FP32 W per site
+W16_BYTES = 43 * 9 * 4           # stored FP16 W per site
+WTC_BYTES = 3216                 # the tensor-core FP16 copy per site (expanded blocks)
 SPINOR64, SPINOR32 = 192, 96
-SPINORDF = 12 * 32               # double-float spinor
 LINKS64 = 4 * 9 * 16
 APPLY64 = W64_BYTES + 2 * SPINOR64            # 6576: W + psi in + out
 APPLY32 = W32_BYTES + 2 * SPINOR32            # 3288
 RESID64 = APPLY64 + SPINOR64                  # true residual also reads b
-# The mixed solve's FP64 true residual runs on the double-float copy: x is converted first (x in,
-# x_df out), then W_df + x_df + b are read and r written.
-RESIDDF = (SPINOR64 + SPINORDF) + WDF_BYTES + SPINORDF + 2 * SPINOR64
-PRECOMPUTE = {"mixed": LINKS64 + WDF_BYTES + W32_BYTES,  # links in, the two W copies out
+PRECOMPUTE = {"mixed": LINKS64 + W64_BYTES + W32_BYTES,  # links in, the FP64-accurate and FP32 W out
               "f64": LINKS64 + W64_BYTES}
 # FP32 vector traffic per BiCGStab iteration: <rhat, v> reads rhat (1); s = r - a v (3);
 # x += a p + w s, r = s - w t with two dots (5 reads + 2 writes); p = r + b (p - w v) (4).
@@ -65,6 +72,10 @@ ITER_VEC64 = (1 + 3 + 7 + 4) * SPINOR64
 # demotion r64 -> r32 with <rhat, r> (3), update of p (4 FP32 vectors).
 RELIABLE32 = 2 * SPINOR64 + 2 * SPINOR32 + (SPINOR64 + 2 * SPINOR32) + 4 * SPINOR32
 RESTART64 = 3 * SPINOR64
+# The tensor-core multi-RHS apply, per site for nrhs right-hand sides: FP16 W (the compact 1548
+# bytes of the stored set) + FP32 fields in and out.
+def tc_apply_bytes(nrhs):
+    return W16_BYTES + nrhs * 2 * SPINOR32
 
 
 def solve_bytes(V, info, mode):
@@ -72,7 +83,7 @@ def solve_bytes(V, info, mode):
     it = info["iters"]
     if mode == "mixed":
         per_iter = 2 * APPLY32 + ITER_VEC32
-        extra = info["fp64_applies"] * RESIDDF + (info["reliable_updates"] + info["restarts"] + 1) * RELIABLE32
+        extra = info["fp64_applies"] * RESID64 + (info["reliable_updates"] + info["restarts"] + 1) * RELIABLE32
     else:
         per_iter = 2 * APPLY64 + ITER_VEC64
         extra = info["fp64_applies"] * RESID64 + (info["restarts"] + 1) * RESTART64
@@ -89,6 +100,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-forms", action="store_true", help="skip the multi_rhs and large solve-form keys")
+    ap.add_argument("--oracle-solve", action="store_true", help="time the oracle's BiCGStab on 16^3 x 32 and exit")
     return ap.parse_args(argv)
 
 
@@ -211,10 +224,12 @@ def ncu_traffic(kernel_key):
 
 def roofline(trace, infos, key, bytes_per_launch, peak, peak_kind, traffic):
     """The roofline record of the apply class `key` from the trace ({class: (launches, ms)}) and the
-    solves' info records.  Every executed iteration applies M twice (v = M p and t = M s); the other
-    launches of the class belong to iterations enqueued after the state halted, which return at once,
-    so the class's whole time is charged to the 2 x iterations launches that do the work."""
-    names = (key + "_dot", key + "_ts")
+    solves' info records.  Every executed iteration applies M twice (v = M p and t = M s; the classes
+    key, key_dot and key_ts: plain or with a fused reduction); the other launches belong to
+    iterations enqueued after the state halted, which return at once, so the classes' whole time is
+    charged to the 2 x iterations launches that do the work.  Only the solves' applies are counted:
+    the timed steps apply M nowhere else."""
+    names = (key, key + "_dot", key + "_ts")
     n_apply = sum(v[0] for k, v in trace.items() if k in names)
     ms_apply = sum(v[1] for k, v in trace.items() if k in names)
     n_work = 2 * sum(i["iters"] for i in infos)
@@ -227,17 +242,69 @@ def roofline(trace, infos, key, bytes_per_launch, peak, peak_kind, traffic):
 
 
 # ----------------------------------------------------------------------------- oracle timing
-def oracle_sample(dims, U, c, b):
-    """One oracle application of M on the full lattice: (seconds, threads used, bytes counted)."""
+def host_cpu():
+    """(logical CPUs, CPU model) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except Exception:
+        pass
+    import platform
+    return os.cpu_count(), model or platform.processor() or platform.machine()
+
+
+def oracle_quads(U, c):
+    """The oracle's 27 W blocks of Eq. minFlopForm, evaluated once (outside any timed region)."""
     from oracle import wform
-    V = dims[0] * dims[1] * dims[2] * dims[3]
+    return wform.quads(U, c)
+
+
+def oracle_sample(quads_, b):
+    """One oracle application of M with W already evaluated: (seconds, threads used)."""
+    from oracle import wform
     c0 = time.process_time()
     t0 = time.perf_counter()
-    wform.apply_lean(U, c, b, (1, 1, 1, 1))
+    wform.apply_quads(quads_, b, (1, 1, 1, 1))
     wall = time.perf_counter() - t0
     cpu = time.process_time() - c0
-    cores = max(1, round(cpu / wall)) if wall > 0 else 1
-    return wall, cores, APPLY64 * V
+    return wall, (max(1, round(cpu / wall)) if wall > 0 else 1)
+
+
+def cpu_baseline(U, c, b, V, reps=5):
+    """The oracle's W-form apply on the host cores: median of `reps` applications, W evaluated once."""
+    q = oracle_quads(U, c)
+    walls, cores = [], 1
+    for _ in range(reps):
+        w, cores = oracle_sample(q, b)
+        walls.append(w)
+    med = statistics.median(walls)
+    nproc, model = host_cpu()
+    return {"value": APPLY64 * V / med / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "nproc": nproc, "cpu_model": model, "seconds": [round(w, 3) for w in walls],
+            "sample": f"median of {reps} oracle applications of M (FP64 numpy, W evaluated once beforehand, "
+                      f"not timed) on the full {WORKLOAD} lattice, {med:.2f} s each, counted as one FP64 apply "
+                      f"({APPLY64} B/site); {cores} of {nproc} host threads used"}
+
+
+def oracle_solve():
+    """The oracle's BiCGStab (FP64 numpy) on the 16^3 x 32 workload to a true residual of 1e-10."""
+    import synth
+    from oracle import bicgstab, wform
+    dims, U, c, b = synth.workload_inputs(WORKLOAD)
+    t0 = time.perf_counter()
+    q = oracle_quads(U, c)
+    tq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x, info = bicgstab.solve(lambda v: wform.apply_quads(q, v, (1, 1, 1, 1)), b, tol=TOL)
+    ts = time.perf_counter() - t0
+    nproc, model = host_cpu()
+    return {"impl": "oracle", "workload": WORKLOAD, "tol": TOL, "solve_s": ts, "w_eval_s": tq,
+            "iters": info["iters"], "true_relres": info["true_relres"], "nproc": nproc, "cpu_model": model}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -272,12 +339,17 @@ def run_ours(args):
     if not args.no_plain and args.mode == "mixed":
         W = ok.precompute_W(U_d, c, bc, ok.W_F64)
         ok.bicgstab(W, b_d, tol=TOL, mode=ok.SOLVE_F64)         # warm-up (module loading, pools)
-        ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev_a.record()
-        _, pinfo = ok.bicgstab(W, b_d, tol=TOL, mode=ok.SOLVE_F64, check_every=CHECK_EVERY)
-        ev_b.record()
-        torch.cuda.synchronize()
-        plain = {"solve_ms": ev_a.elapsed_time(ev_b), "iters": pinfo["iters"], "true_relres": pinfo["true_relres"]}
+        times = []
+        for _ in range(5):
+            ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev_a.record()
+            _, pinfo = ok.bicgstab(W, b_d, tol=TOL, mode=ok.SOLVE_F64, check_every=CHECK_EVERY)
+            ev_b.record()
+            torch.cuda.synchronize()
+            times.append(ev_a.elapsed_time(ev_b))
+        plain = {"solve_ms": statistics.median(times), "solve_ms_all": [round(t, 3) for t in times],
+                 "timed_solves": len(times), "iters": pinfo["iters"], "true_relres": pinfo["true_relres"],
+                 "residuals": "native FP64 W on the FP64 pipe"}
         W.free()
 
     for _ in range(args.warmup):
@@ -345,14 +417,13 @@ def run_ours(args):
                "h2d_bytes_per_step": U_h.numel() * U_h.element_size() + b_h.numel() * b_h.element_size(),
                "d2h_bytes_per_step": x_h.numel() * x_h.element_size()}
 
+    forms = {} if args.no_forms else run_forms(ok, torch, dev, peak, peak_kind)
+
     if rank != 0:
         return None
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        wall, cores, nbytes = oracle_sample(dims, U, c, b)
-        cpu = {"value": nbytes / wall / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
-               "sample": f"one oracle application of M (W formulas re-evaluated inside, FP64 numpy) on the full "
-                         f"{WORKLOAD} lattice, {wall:.1f} s, counted as one FP64 apply ({APPLY64} B/site)"}
+        cpu = cpu_baseline(U, c, b, V)
     iters = [i["iters"] for i in infos]
     solve_ms = statistics.median(i["time_ms"] for i in infos)
     line = {
@@ -366,8 +437,10 @@ def run_ours(args):
                    "step": ("precompute W (double-float FP64 + FP32) + solve to 1e-10 true residual + free W"
                             if args.mode == "mixed" else "precompute W (FP64) + solve to 1e-10 true residual + free W"),
                    "l2": "inputs larger than L2 (W = %.2f GB per step)" % (
-                       V * ((WDF_BYTES + W32_BYTES) if args.mode == "mixed" else W64_BYTES) / 1e9),
+                       V * ((2 * W64_BYTES + W32_BYTES) if args.mode == "mixed" else W64_BYTES) / 1e9),
                    "parallelism": f"replicas x{world}"},
+        "value_is": ("algorithmic HBM bytes of the whole step (precompute + solve to 1e-10 + release) per second; "
+                     "the M.psi GB/s of the dominant apply is roofline.achieved"),
         "roofline": roof,
         "percent_of_hbm_peak": 100.0 * value / peak,
         "kernel_time_shares": shares,
@@ -377,7 +450,96 @@ def run_ours(args):
         "time_to_solution_ratio_plain_over_chosen": (plain["solve_ms"] / solve_ms) if plain else None,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
     }
+    line.update(forms)
     return line
+
+
+# ----------------------------------------------------------------------------- solve forms
+def _spin_colour_sources(torch, dims, dev):
+    """The 12 unit sources at site 0 (spin s, colour c -> source 3 s + c), [12, ..., 4, 3] complex128."""
+    import synth
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    b = torch.zeros((12, V, 12), dtype=torch.complex128, device=dev)
+    for k in range(12):
+        b[k, 0, k] = 1.0
+    return b.reshape((12,) + synth.lattice_shape(dims) + (4, 3))
+
+
+def _events_ms(torch, fn):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    out = fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), out
+
+
+def solve_form(ok, torch, dev, name, dims, eps, seed, am0, peak, peak_kind, delta=1e-4, tc_roofline=False):
+    """Time to a true FP64 residual below 1e-10 for the 12 spin-colour point sources of one
+    propagator: one lockstep multi-RHS solve on the tensor cores (FP16 operands, FP32 accumulation
+    and vectors, FP64 reliable updates with double-float residuals, graph-captured iterations)
+    against plain FP64 BiCGStab, timed on two of the sources and scaled to twelve."""
+    import synth
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    c = synth.placeholder_coeffs(am0)
+    bc = (1, 1, 1, 1)
+    U = synth.device_random_links(dims, eps, seed, device=dev)
+    b = _spin_colour_sources(torch, dims, dev)
+    free0, total = torch.cuda.mem_get_info()
+    Wc = ok.precompute_W(U, c, bc, ok.W_DF64 | ok.W_F16_TC)
+    ok.bicgstab_multi(Wc, b[:2].contiguous(), tol=1e-2, mode=ok.SOLVE_MIXED_TC, delta=delta)   # warm-up
+    ok.trace_reset()
+    ok.trace_enable(True)
+    ms, (x, infos) = _events_ms(torch, lambda: ok.bicgstab_multi(Wc, b, tol=TOL, mode=ok.SOLVE_MIXED_TC, delta=delta,
+                                                                 check_every=8))
+    ok.trace_enable(False)
+    trace = ok.trace_read()
+    free1, _ = torch.cuda.mem_get_info()
+    resid = [ok.true_residual(Wc, b[k].contiguous(), x[k].contiguous()) for k in range(12)]
+    del x
+    Wc.free()
+    Wp = ok.precompute_W(U, c, bc, ok.W_F64)
+    ok.bicgstab(Wp, b[0].contiguous(), tol=1e-2, mode=ok.SOLVE_F64)                             # warm-up
+    plain_ms, plain_it = [], []
+    for k in (0, 11):
+        t, (_, pinfo) = _events_ms(torch, lambda: ok.bicgstab(Wp, b[k].contiguous(), tol=TOL, mode=ok.SOLVE_F64,
+                                                              check_every=CHECK_EVERY))
+        plain_ms.append(t)
+        plain_it.append(pinfo["iters"])
+    Wp.free()
+    plain12 = 6.0 * sum(plain_ms)
+    out = {"workload": name, "sites": V, "links_eps": eps, "am0": am0, "sources": 12, "tol": TOL,
+           "links": "drawn on the device (torch seeded generator, the host recipe's distribution)",
+           "form": "multi-RHS tensor-core BiCGStab (FP16 operands, FP32 accumulation and vectors, FP64 reliable "
+                   f"updates on the double-float W, delta {delta}, graph-captured iterations)",
+           "chosen_ms": ms, "iters": [i["iters"] for i in infos], "reliable_updates": [i["reliable_updates"] for i in infos],
+           "true_relres_max": max(resid),
+           "plain_fp64_ms": [round(t, 3) for t in plain_ms], "plain_fp64_iters": plain_it,
+           "plain_fp64_timed_solves": 2, "plain_fp64_ms_12_scaled": plain12,
+           "ratio_plain_over_chosen": plain12 / ms,
+           "device_memory_in_use_gb": round((total - min(free0, free1)) / 1e9, 2) if free1 < free0 else None,
+           "device_memory_held_by_solve_gb": round((free0 - free1) / 1e9, 2)}
+    if tc_roofline:
+        names = ("apply_tc_dot", "apply_tc_ts")
+        n = sum(v[0] for k, v in trace.items() if k in names)
+        t_ms = sum(v[1] for k, v in trace.items() if k in names)
+        if n:
+            us = t_ms / n * 1e3
+            ach = tc_apply_bytes(12) * V / (us * 1e-6) / 1e9
+            out["roofline_tc"] = {"kernel": "apply_tc (12 right-hand sides)", "bound": "hbm", "achieved": ach,
+                                  "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                                  "traffic": None, "algorithmic_bytes_per_launch": tc_apply_bytes(12) * V,
+                                  "stored_w_bytes_per_site": WTC_BYTES, "launches": n, "avg_launch_us": us,
+                                  "timed": "CUDA events around the directly launched iterations of the solve "
+                                           "(before its graph replays)"}
+    return out
+
+
+def run_forms(ok, torch, dev, peak, peak_kind):
+    return {"multi_rhs": solve_form(ok, torch, dev, "20^3x64", (20, 20, 20, 64), 0.2, 13115031, 1.0, peak, peak_kind,
+                                    tc_roofline=True),
+            "large": solve_form(ok, torch, dev, "28^3x96", (28, 28, 28, 96), 0.15, 13115032, 0.8, peak, peak_kind)}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -388,26 +550,32 @@ def run_reference(args):
         return None
     dims, U, c, b = synth.workload_inputs(WORKLOAD)
     V = dims[0] * dims[1] * dims[2] * dims[3]
+    q = oracle_quads(U, c)
     for _ in range(args.warmup):
-        oracle_sample(dims, U, c, b)
+        oracle_sample(q, b)
     walls, cores = [], 1
     for _ in range(args.steps):
-        w, cores, nbytes = oracle_sample(dims, U, c, b)
+        w, cores = oracle_sample(q, b)
         walls.append(w)
     total = sum(walls)
     value = args.steps * APPLY64 * V / total / 1e9
-    sample = (f"each step one oracle application of M (FP64 numpy, W formulas re-evaluated inside) on the full "
+    nproc, model = host_cpu()
+    sample = (f"each step one oracle application of M (FP64 numpy, W evaluated once before the steps) on the full "
               f"{WORKLOAD} lattice, counted as one FP64 apply ({APPLY64} B/site)")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "lattice_xyzt": list(dims), "sites": V},
-            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "nproc": nproc, "cpu_model": model},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main(argv=None):
     args = parse_args(argv)
+    if args.oracle_solve:
+        print(json.dumps(oracle_solve()), flush=True)
+        return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)

@@ -10,17 +10,24 @@ import bench
 
 
 def test_byte_model():
+    """Each stored byte read once and each output written once; FP64-accurate work at FP64 bytes
+    whatever carries it (the double-float copy is charged as the 6192-byte FP64 W per site)."""
     assert bench.APPLY32 == 3288 and bench.APPLY64 == 6576
-    assert bench.W32_BYTES == 43 * 9 * 8 and bench.WDF_BYTES == 2 * bench.W64_BYTES
-    # double-float residual: x converted (192 in, 384 out), W_df + x_df + b read, r written
-    assert bench.RESIDDF == 192 + 384 + 12384 + 384 + 2 * 192
-    assert bench.PRECOMPUTE["mixed"] == 576 + 12384 + 3096 and bench.PRECOMPUTE["f64"] == 576 + 6192
+    assert bench.W64_BYTES == 6192 and bench.W32_BYTES == 43 * 9 * 8 and bench.W16_BYTES == 1548
+    assert bench.RESID64 == 6576 + 192
+    assert bench.PRECOMPUTE["mixed"] == 576 + 6192 + 3096 and bench.PRECOMPUTE["f64"] == 576 + 6192
+    assert bench.tc_apply_bytes(12) == 1548 + 12 * (96 + 96)
     info = dict(iters=10, fp64_applies=2, reliable_updates=1, restarts=0)
     V = 1000
-    expect = V * (10 * (2 * 3288 + bench.ITER_VEC32) + 2 * bench.RESIDDF + 2 * bench.RELIABLE32)
+    expect = V * (10 * (2 * 3288 + bench.ITER_VEC32) + 2 * bench.RESID64 + 2 * bench.RELIABLE32)
     assert bench.solve_bytes(V, info, "mixed") == expect
     assert bench.solve_bytes(V, dict(iters=0, fp64_applies=0, reliable_updates=0, restarts=0), "f64") == \
         V * bench.RESTART64
+
+
+def test_host_cpu_record():
+    nproc, model = bench.host_cpu()
+    assert isinstance(nproc, int) and nproc >= 1 and isinstance(model, str) and model
 
 
 def test_reduce_without_process_group():
@@ -66,7 +73,7 @@ def test_two_rank_max_time_sum_units():
 
 def test_reference_arm_line(capsys):
     """`bench.py --impl reference` times the oracle on the host and prints the contract's JSON line
-    (one step on the full workload, about ten seconds of CPU)."""
+    (W evaluated once, then one step on the full workload: about half a minute of CPU)."""
     import json
     bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0"])
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
@@ -74,6 +81,7 @@ def test_reference_arm_line(capsys):
     assert line["higher_is_better"] is True and line["steps"] == 1 and line["n_gpus"] == 1
     assert line["config"]["workload"] == bench.WORKLOAD and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["nproc"] >= 1 and line["cpu_baseline"]["cpu_model"]
     assert line["e2e"] == {"value": line["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
