@@ -53,8 +53,10 @@ typedef struct {
 /* Precision of an application of M: OK_F64 (complex128 fields, FP64-accurate W), OK_F32 (complex64
  * fields, FP32 W), OK_F32_W16 (complex64 fields and FP32 arithmetic with the FP16 copy of W) or
  * OK_F16_TC (several right-hand sides at once on the tensor cores: complex64 fields and the
- * OK_W_F16_TC copy of W enter the products as FP16, which accumulate in FP32). */
-typedef enum { OK_F64 = 0, OK_F32 = 1, OK_F32_W16 = 2, OK_F16_TC = 3 } ok_prec;
+ * OK_W_F16_TC copy of W enter the products as FP16, which accumulate in FP32) or OK_F32_OTF
+ * (complex64 fields; no stored W: each W matrix of Eqs. shifted_W_first .. shifted_W_last is
+ * rebuilt in FP32 from the links and clover fields of an OK_W_OTF handle where a hop needs it). */
+typedef enum { OK_F64 = 0, OK_F32 = 1, OK_F32_W16 = 2, OK_F16_TC = 3, OK_F32_OTF = 4 } ok_prec;
 
 /* Which stored copies a W handle carries (bit mask for ok_precompute_W).  OK_W_DF64 keeps FP64
  * accuracy as double-float pairs (hi + lo, two floats, about 48 significand bits): FP64 applications
@@ -73,6 +75,9 @@ typedef enum { OK_F64 = 0, OK_F32 = 1, OK_F32_W16 = 2, OK_F16_TC = 3 } ok_prec;
  * (u - l) / sqrt 2 of the neighbour spinor, each entry rounded once from FP64 (relative 2^-11);
  * 3216 bytes per site, in a site-major layout. */
 #define OK_W_F16_TC 32
+/* Inputs of the on-the-fly apply (OK_F32_OTF) instead of a stored W: FP32 copies of the links
+ * (288 bytes per site) and of the clover fields E_k, B_k (432 bytes per site), site-blocked. */
+#define OK_W_OTF 64
 
 /* Coefficients of the tree-level, tadpole-improved OK action (Sec. 1; they enter the W formulas,
  * Eqs. shifted_W_first .. shifted_W_last).  u0 <= 0: u0 is computed from the mean plaquette of
@@ -151,7 +156,9 @@ int ok_W_info(const ok_W* W, ok_lattice* lat, int* W_precs, size_t* bytes);
 /* out = M psi (Eq. dslash with M in the form of Eq. minFlopForm: the on-site W^0, the 8 nearest,
  * 6 next-to-nearest straight and 12 diagonal neighbours), using the handle's stored matrices of
  * precision `prec`, arithmetic in that precision (OK_F32_W16: complex64 fields, FP32 arithmetic,
- * matrices read from the OK_W_F16 copy and widened to FP32).
+ * matrices read from the OK_W_F16 copy and widened to FP32; OK_F32_OTF: complex64 fields, no stored
+ * matrices: each W group of a hop is rebuilt in FP32 from the OK_W_OTF links and clover fields, at
+ * x for a forward hop and at the neighbour for a backward one, Sec. 2.2's precalculation undone).
  *   psi, out: device [V][4][3] complex in `prec`; out must not overlap psi.
  * Errors: OK_EINVAL (null, aliasing, handle lacks `prec`), OK_ECUDA.  Asynchronous. */
 int ok_apply_M(const ok_W* W, ok_prec prec, const void* psi, void* out, void* stream);

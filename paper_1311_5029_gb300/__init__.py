@@ -23,11 +23,11 @@ __all__ = [
     "load", "precompute_W", "apply_M", "bicgstab", "true_residual", "W_expand", "launch_count",
     "strerror", "OKError", "WHandle", "F64", "F32", "F32_W16", "W_F64", "W_F32", "W_DF64", "W_F16", "W_LINKS", "Net", "net_create", "net_apply", "net_loss_grad", "net_train_step", "bicgstab_net",
     "SOLVE_AUTO", "SOLVE_F64", "SOLVE_MIXED", "SOLVE_MIXED16", "header_functions", "wait_timeouts", "apply_M_multi", "bicgstab_multi", "autotune", "set_launch_shape", "trace_enable", "trace_read", "trace_reset", "true_residual_static",
-    "apply_M_reduce", "REDUCE_DOT", "REDUCE_TS", "F16_TC", "W_F16_TC", "SOLVE_MIXED_TC", "SOLVE_DEFECT",
+    "apply_M_reduce", "REDUCE_DOT", "REDUCE_TS", "F16_TC", "W_F16_TC", "SOLVE_MIXED_TC", "SOLVE_DEFECT", "F32_OTF", "W_OTF",
 ]
 
-F64, F32, F32_W16, F16_TC = 0, 1, 2, 3
-W_F64, W_F32, W_DF64, W_F16, W_LINKS, W_F16_TC = 1, 2, 4, 8, 16, 32
+F64, F32, F32_W16, F16_TC, F32_OTF = 0, 1, 2, 3, 4
+W_F64, W_F32, W_DF64, W_F16, W_LINKS, W_F16_TC, W_OTF = 1, 2, 4, 8, 16, 32, 64
 SOLVE_AUTO, SOLVE_F64, SOLVE_MIXED, SOLVE_MIXED16, SOLVE_MIXED_TC = 0, 1, 2, 3, 4
 SOLVE_DEFECT = 8   # flag: outer defect correction (or with a low-precision mode)
 OK_ENOCONV, OK_EBREAKDOWN = -4, -5
@@ -264,7 +264,8 @@ def _field_check(W: WHandle, t, name):
 
 def apply_M(W: WHandle, psi, out=None, stream=None, prec=None):
     """ok_apply_M: out = M psi in the precision of psi (complex128 -> FP64, complex64 -> FP32).
-    prec=F32_W16 (complex64 fields) applies with the half-precision W copy."""
+    prec=F32_W16 (complex64 fields) applies with the half-precision W copy; prec=F32_OTF (complex64
+    fields, a handle with W_OTF) rebuilds W from the links and clover fields inside the apply."""
     import torch
     _field_check(W, psi, "psi")
     if out is None:

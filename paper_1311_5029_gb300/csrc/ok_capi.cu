@@ -106,7 +106,7 @@ void ok_free_W(ok_W* W) {
   if (!W) return;
   // Returned to the stream-ordered pool they came from, after the work already queued on the
   // legacy default stream (the caller guarantees that no work on the handle is pending).
-  for (void* q : {W->W64, W->W32, W->Wdf, W->W16, W->L32, W->Wtc})
+  for (void* q : {W->W64, W->W32, W->Wdf, W->W16, W->L32, W->Wtc, W->EB32})
     if (q) cudaFreeAsync(q, 0);
   delete W;
 }
@@ -125,7 +125,7 @@ int ok_W_info(const ok_W* W, ok_lattice* lat, int* W_precs, size_t* bytes) {
 
 int ok_apply_M(const ok_W* W, ok_prec prec, const void* psi, void* out, void* stream) {
   if (!W || !psi || !out) return OK_EINVAL;
-  size_t es = prec == OK_F64 ? 16 : (prec == OK_F32 || prec == OK_F32_W16) ? 8 : 0;
+  size_t es = prec == OK_F64 ? 16 : (prec == OK_F32 || prec == OK_F32_W16 || prec == OK_F32_OTF) ? 8 : 0;
   if (es == 0) return OK_EINVAL;
   size_t bytes = (size_t)W->g.V * 12 * es;
   const char* a = (const char*)psi;
@@ -152,6 +152,7 @@ int ok_apply_M(const ok_W* W, ok_prec prec, const void* psi, void* out, void* st
     return rc;
   }
   EpiArgs<float> e{};
+  if (prec == OK_F32_OTF) return launch_apply_otf(W, (const cx<float>*)psi, (cx<float>*)out, (cudaStream_t)stream);
   if (prec == OK_F32_W16) {
     if (!W->W16) return OK_EINVAL;
     return launch_apply_w16(W, (const cx<float>*)psi, (cx<float>*)out, EPI_NONE, e, (cudaStream_t)stream);

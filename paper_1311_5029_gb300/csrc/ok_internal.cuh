@@ -191,12 +191,14 @@ struct ok_W {
   ok_lattice lat;
   int precs;
   okgb::WScalars sc;
+  ok_coeffs coeffs;  // as given to ok_precompute_W (the on-the-fly apply evaluates the W formulas)
   void* W64;     // cx<double>[nblk * SITE_ELEMS * 32]
   void* W32;     // cx<float>[...]
   void* Wdf;     // cx<dd>[...]: FP64-accurate double-float copy
   void* W16;     // cx<__half>[...]: half-precision copy
   void* L32;     // cx<float>[nblk][4][9][32]: FP32 links, site-blocked (OK_W_LINKS), for the preconditioner network
   void* Wtc;     // [V][804] FP16 complex words: blocks of the tensor-core apply (OK_W_F16_TC, ok_tc.cu)
+  void* EB32;    // cx<float>[nblk][6][9][32]: FP32 clover fields E_k, B_k, site-blocked (OK_W_OTF)
   size_t bytes;
   int device;
   mutable okgb::Tune tune;

@@ -26,6 +26,9 @@ int launch_apply(const ok_W* W, const cx<R>* psi, cx<R>* out, int epi, const Epi
 int apply_blocks_needed(const ok_W* W);
 // FP32 fields and arithmetic with the half-precision W copy (all epilogues).
 int launch_apply_w16(const ok_W* W, const cx<float>* psi, cx<float>* out, int epi, const EpiArgs<float>& ep, cudaStream_t st);
+// out = M psi in FP32 with every W matrix rebuilt from the handle's FP32 links and clover fields
+// (OK_W_OTF) inside the apply; OK_EINVAL without them.
+int launch_apply_otf(const ok_W* W, const cx<float>* psi, cx<float>* out, cudaStream_t st);
 // Bounded device waits that gave up (the kernel's result is then invalid); optionally reset.
 int read_wait_timeouts(unsigned* n, bool reset);
 int set_stage_test_bytes(unsigned bytes);  // failure injection for the bounded waits

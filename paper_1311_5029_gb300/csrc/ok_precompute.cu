@@ -19,44 +19,10 @@
 //   opp_diag_pre_mat inside the apply.
 #include "ok_launch.cuh"
 #include "ok_split.cuh"
+#include "ok_wform.cuh"
 #include <new>
 
 namespace okgb {
-
-// ---------------------------------------------------------------------------- indexing
-__device__ __forceinline__ int wrapi(int x, int L) {
-  int r = x % L;
-  return r < 0 ? r + L : r;
-}
-
-struct Site {
-  int c[4];
-};
-
-__device__ __forceinline__ Site site_coords(int s, const Geom& g) {
-  Site p;
-  p.c[0] = s % g.L[0]; s /= g.L[0];
-  p.c[1] = s % g.L[1]; s /= g.L[1];
-  p.c[2] = s % g.L[2]; s /= g.L[2];
-  p.c[3] = s;
-  return p;
-}
-
-// Site index of x + (d0, d1, d2, d3) with periodic wrapping (gauge fields are periodic).
-__device__ __forceinline__ int nbr(const Site& p, const Geom& g, int d0, int d1, int d2, int d3) {
-  int x = wrapi(p.c[0] + d0, g.L[0]);
-  int y = wrapi(p.c[1] + d1, g.L[1]);
-  int z = wrapi(p.c[2] + d2, g.L[2]);
-  int t = wrapi(p.c[3] + d3, g.L[3]);
-  return x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
-}
-
-__device__ __forceinline__ int nbr_dir(const Site& p, const Geom& g, int mu, int n, int nu = 0, int m = 0) {
-  int d[4] = {0, 0, 0, 0};
-  d[mu] += n;
-  d[nu] += m;
-  return nbr(p, g, d[0], d[1], d[2], d[3]);
-}
 
 template <typename LT>
 __device__ __forceinline__ M3<double> load_link(const cx<LT>* __restrict__ U, int site, int mu) {
@@ -196,14 +162,20 @@ __device__ __forceinline__ void store_mat(const WOut& o, int site, int m, const 
   }
 }
 
-__device__ __forceinline__ int levi(int i, int j, int k) {
-  if (i == j || j == k || i == k) return 0;
-  return ((j - i + 3) % 3 == 1) ? 1 : -1;
-}
-
 constexpr int K2_THREADS = 64;
 
-// part 0: W^0 and W^+_4; parts 1..3: W^+_i for i = part - 1; part 4: W^{++}_ii, W^{++}_ij, W^{+-}_ij.
+// The inputs of the W formulas in the precompute: canonical links (FP64 or FP32) and the FP64 clover
+// fields of clover_kernel.
+template <typename LT>
+struct CanonInputs {
+  const cx<LT>* __restrict__ links;
+  const cx<double>* __restrict__ EB;
+  __device__ __forceinline__ M3<double> U(int site, int mu) const { return load_link(links, site, mu); }
+  __device__ __forceinline__ M3<double> F(int site, int k) const { return load_eb(EB, site, k); }
+};
+
+// part 0: W^0 and W^+_4; parts 1..3: W^+_i for i = part - 1; part 4: W^{++}_ii, W^{++}_ij, W^{+-}_ij
+// (the formulas are those of ok_wform.cuh, in FP64).
 template <typename LT>
 __global__ void __launch_bounds__(K2_THREADS) w_kernel(const cx<LT>* __restrict__ U,
                                                        const cx<double>* __restrict__ EB, Geom g,
@@ -211,123 +183,38 @@ __global__ void __launch_bounds__(K2_THREADS) w_kernel(const cx<LT>* __restrict_
                                                        WOut o, int part) {
   int s = blockIdx.x * K2_THREADS + threadIdx.x;
   if (s >= g.V) return;
-  const WScalars sc = *scp;
-  const double u0 = sc.u0;
-  const double u03 = u0 * u0 * u0, u04 = u03 * u0;
-  Site p = site_coords(s, g);
-  const cx<double> I = mk<double>(0.0, 1.0);
-
+  const double u0 = scp->u0;
+  const Site p = site_coords(s, g);
+  const CanonInputs<LT> in{U, EB};
   if (part == 0) {
-    // W^0: D0 = -(c_B zeta + 16 c5)/(2 u0^3) i sum sigma_k B_k, S0 = -(c_E zeta)/(2 u0^3) sum sigma_k E_k
-    const double cd = -(c.c_B * c.zeta + 16.0 * c.c5) / (2.0 * u03);
-    const double cs = -(c.c_E * c.zeta) / (2.0 * u03);
-    M3<double> yp[3], ym[3];
-    for (int k = 0; k < 3; ++k) {
-      M3<double> d = m_scale(mk<double>(0.0, cd), load_eb(EB, s, 3 + k));   // i cd B_k
-      M3<double> e = m_rscale(cs, load_eb(EB, s, k));                      // cs E_k
-      M3<double> ie = m_scale(I, e);
-      yp[k] = m_rscale(0.25, m_add(d, ie));
-      ym[k] = m_rscale(0.25, m_sub(d, ie));
+    M3<double> yp[3], ym[3], t[3], uh;
+    wform::onsite<double>(in, s, c, u0, yp, ym);
+    for (int j = 0; j < 3; ++j) {
+      store_mat(o, s, M_Y0P + j, yp[j]);
+      store_mat(o, s, M_Y0M + j, ym[j]);
     }
-    // [[y_z, y_x - i y_y], [y_x + i y_y, -y_z]]
-    store_mat(o, s, M_Y0P + 0, yp[2]);
-    store_mat(o, s, M_Y0P + 1, m_sub(yp[0], m_scale(I, yp[1])));
-    store_mat(o, s, M_Y0P + 2, m_add(yp[0], m_scale(I, yp[1])));
-    store_mat(o, s, M_Y0M + 0, ym[2]);
-    store_mat(o, s, M_Y0M + 1, m_sub(ym[0], m_scale(I, ym[1])));
-    store_mat(o, s, M_Y0M + 2, m_add(ym[0], m_scale(I, ym[1])));
-    // W^+_4: S4 = c_EE/(2 u0^4) (U_t E(x+t) - E(x) U_t), sum over sigma_k
-    M3<double> Ut = load_link(U, s, 3);
-    int st = nbr_dir(p, g, 3, 1);
-    const double ct = c.c_EE / (2.0 * u04);
-    M3<double> tk[3];
-    for (int k = 0; k < 3; ++k)
-      tk[k] = m_rscale(0.5 * ct, m_sub(m_mul(Ut, load_eb(EB, st, k)), m_mul(load_eb(EB, s, k), Ut)));
-    store_mat(o, s, M_UT, m_rscale(0.5, Ut));
-    store_mat(o, s, M_ST + 0, tk[2]);
-    store_mat(o, s, M_ST + 1, m_sub(tk[0], m_scale(I, tk[1])));
-    store_mat(o, s, M_ST + 2, m_add(tk[0], m_scale(I, tk[1])));
+    wform::temporal<double>(in, p, g, s, c, u0, uh, t);
+    store_mat(o, s, M_UT, uh);
+    for (int j = 0; j < 3; ++j) store_mat(o, s, M_ST + j, t[j]);
     return;
   }
-
   if (part >= 1 && part <= 3) {
     const int i = part - 1;
-    M3<double> Ui = load_link(U, s, i);
-    int si = nbr_dir(p, g, i, 1);
-    M3<double> Bx[3], Bxi[3];
-    for (int k = 0; k < 3; ++k) {
-      Bx[k] = load_eb(EB, s, 3 + k);
-      Bxi[k] = load_eb(EB, si, 3 + k);
-    }
-    // S^+_i = 1 (x) b0 + sum_l sigma_l (x) b_l
-    const double c3f = c.c3 / (2.0 * u04);
-    M3<double> b[4];
-    b[0] = m_scale(mk<double>(0.0, c3f), m_add(m_mul(Ui, Bxi[i]), m_mul(Bx[i], Ui)));
-    for (int l = 0; l < 3; ++l) {
-      M3<double> acc = (l == i) ? m_rscale(0.5 * (c.zeta - 2.0 * c.c1 - 12.0 * c.c2), Ui) : m_zero<double>();
-      for (int k = 0; k < 3; ++k) {
-        int e = levi(i, k, l);
-        if (e == 0) continue;
-        acc = m_sub(acc, m_rscale(c3f * e, m_sub(m_mul(Ui, Bxi[k]), m_mul(Bx[k], Ui))));
-      }
-      b[1 + l] = acc;
-    }
-    // D^+_i = 1 (x) a0 + sum_l sigma_l (x) a_l
-    M3<double> a[4];
-    a[0] = m_rscale(-0.5 * (c.r_s * c.zeta + 8.0 * c.c4), Ui);
-    const double cst = 0.25 * c.c5 * (1.0 / (u0 * u0) - 1.0 / u04);
-    const double c5f = c.c5 / u04;
-    M3<double> staple[3];
-    for (int k = 0; k < 3; ++k) {
-      if (k == i) { staple[k] = m_zero<double>(); continue; }
-      // U_k(x) U_i(x+k) U_k(x+i)^dag - U_k(x-k)^dag U_i(x-k) U_k(x-k+i)
-      M3<double> up = m_mul(m_mul(load_link(U, s, k), load_link(U, nbr_dir(p, g, k, 1), i)),
-                            m_dag(load_link(U, si, k)));
-      int smk = nbr_dir(p, g, k, -1);
-      M3<double> dn = m_mul(m_mul(m_dag(load_link(U, smk, k)), load_link(U, smk, i)),
-                            load_link(U, nbr_dir(p, g, k, -1, i, 1), k));
-      staple[k] = m_sub(up, dn);
-    }
-    for (int l = 0; l < 3; ++l) {
-      M3<double> acc = m_zero<double>();
-      for (int k = 0; k < 3; ++k) {
-        int e = levi(i, l, k);
-        if (e == 0) continue;
-        acc = m_add(acc, m_scale(mk<double>(0.0, cst * e), staple[k]));
-      }
-      if (l != i) acc = m_add(acc, m_scale(mk<double>(0.0, c5f), m_add(m_mul(Ui, Bxi[l]), m_mul(Bx[l], Ui))));
-      a[1 + l] = acc;
-    }
-    // blocks of (D +- S)/2: 00 = q0 + q3, 01 = q1 - i q2, 10 = q1 + i q2, 11 = q0 - q3
-    for (int sg = 0; sg < 2; ++sg) {
-      M3<double> q[4];
-      for (int k = 0; k < 4; ++k) q[k] = m_rscale(0.5, sg == 0 ? m_add(a[k], b[k]) : m_sub(a[k], b[k]));
-      int base = M_WP + 8 * i + 4 * sg;
-      store_mat(o, s, base + 0, m_add(q[0], q[3]));
-      store_mat(o, s, base + 1, m_sub(q[1], m_scale(I, q[2])));
-      store_mat(o, s, base + 2, m_add(q[1], m_scale(I, q[2])));
-      store_mat(o, s, base + 3, m_sub(q[0], q[3]));
-    }
+    M3<double> q[8];
+    wform::spatial<double>(in, p, g, s, i, c, u0, q);
+    for (int k = 0; k < 8; ++k) store_mat(o, s, M_WP + 8 * i + k, q[k]);
     return;
   }
-
   // part 4: two-hop colour matrices
-  M3<double> Ul[3];
-  for (int i = 0; i < 3; ++i) Ul[i] = load_link(U, s, i);
-  for (int i = 0; i < 3; ++i) store_mat(o, s, M_VII + i, m_mul(Ul[i], load_link(U, nbr_dir(p, g, i, 1), i)));
-  const double cij = c.c2 / (4.0 * u0);
+  for (int i = 0; i < 3; ++i) store_mat(o, s, M_VII + i, wform::twohop<double>(in, p, g, s, i));
   int pr = 0;
   for (int i = 0; i < 3; ++i) {
     for (int j = i + 1; j < 3; ++j, ++pr) {
-      // U_i(x) U_j(x+i) + U_j(x) U_i(x+j)
-      M3<double> v = m_add(m_mul(Ul[i], load_link(U, nbr_dir(p, g, i, 1), j)),
-                           m_mul(Ul[j], load_link(U, nbr_dir(p, g, j, 1), i)));
-      store_mat(o, s, M_VIJ + pr, m_rscale(cij, v));
-      // U_i(x) U_j(x-j+i)^dag + U_j(x-j)^dag U_i(x-j)
-      int smj = nbr_dir(p, g, j, -1);
-      M3<double> x = m_add(m_mul(Ul[i], m_dag(load_link(U, nbr_dir(p, g, j, -1, i, 1), j))),
-                           m_mul(m_dag(load_link(U, smj, j)), load_link(U, smj, i)));
-      store_mat(o, s, M_XIJ + pr, m_rscale(cij, x));
+      M3<double> v, x;
+      wform::diag_v<double>(in, p, g, s, i, j, c, u0, v);
+      wform::diag_x<double>(in, p, g, s, i, j, c, u0, x);
+      store_mat(o, s, M_VIJ + pr, v);
+      store_mat(o, s, M_XIJ + pr, x);
     }
   }
 }
@@ -501,7 +388,8 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
   OK_LAUNCH_CHECK();
   WOut o{W->W64 ? (cx<double>*)W->W64 : W64tmp, (cx<float>*)W->W32, (cx<dd>*)W->Wdf, (cx<__half>*)W->W16};
   int nb2 = grid_for(g.V, K2_THREADS);
-  for (int part_id = 0; part_id < 5; ++part_id) {
+  const bool any_w = o.W64 || o.W32 || o.Wdf || o.W16;  // (a handle for the on-the-fly apply stores none)
+  for (int part_id = 0; any_w && part_id < 5; ++part_id) {
     {
     TraceScope ts("w_build", st);
     w_kernel<LT><<<nb2, K2_THREADS, 0, st>>>(U, EB, g, *c, dsc, o, part_id);
@@ -509,6 +397,17 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
     OK_LAUNCH_CHECK();
   }
   return OK_SUCCESS;
+}
+
+// Clover fields (FP64, [V][6][9]) -> the FP32 copy of an OK_W_OTF handle, site-blocked like W:
+// element e of field k (E_0..2, B_0..2) of the site in lane l of block blk at ((blk * 6 + k) * 9 + e) * 32 + l.
+__global__ void eb_blocked_kernel(const cx<double>* __restrict__ in, cx<float>* __restrict__ out, int V) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;  // (site, k, e) in input order
+  if (i >= 54LL * V) return;
+  const int site = (int)(i / 54), r = (int)(i % 54);
+  const int k = r / 9, e = r % 9;
+  const cx<double> u = in[i];
+  out[(((size_t)(site >> 5) * 6 + k) * 9 + e) * LANES + (site & 31)] = mk<float>((float)u.re, (float)u.im);
 }
 
 // Links -> the FP32 copy kept in the handle (OK_W_LINKS), in the site-blocked layout of W:
@@ -546,8 +445,8 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
                int precs, cudaStream_t st, ok_W** W_out) {
   if (!lat || !links || !c || !W_out) return OK_EINVAL;
   if (links_prec != OK_F64 && links_prec != OK_F32) return OK_EINVAL;
-  if ((precs & (OK_W_F64 | OK_W_F32 | OK_W_DF64 | OK_W_F16 | OK_W_F16_TC)) == 0 ||
-      (precs & ~(OK_W_F64 | OK_W_F32 | OK_W_DF64 | OK_W_F16 | OK_W_LINKS | OK_W_F16_TC)))
+  if ((precs & (OK_W_F64 | OK_W_F32 | OK_W_DF64 | OK_W_F16 | OK_W_F16_TC | OK_W_OTF)) == 0 ||
+      (precs & ~(OK_W_F64 | OK_W_F32 | OK_W_DF64 | OK_W_F16 | OK_W_LINKS | OK_W_F16_TC | OK_W_OTF)))
     return OK_EINVAL;
   if (!(c->u0 > 0.0) && c->u0 > 0.0) return OK_EINVAL;
   *W_out = nullptr;
@@ -558,6 +457,7 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
   W->g = g;
   W->lat = *lat;
   W->precs = precs;
+  W->coeffs = *c;
   OK_CUDA_TRY(cudaGetDevice(&W->device));
   size_t elems = (size_t)g.nblk * SITE_ELEMS * LANES;
   // Stream-ordered allocations (cheap when the pool already holds the memory, e.g. one handle per
@@ -570,7 +470,7 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
   WScalars* dsc = nullptr;
   void* W64tmp = nullptr;  // FP64 matrices for the tensor-core copy when OK_W_F64 is not kept
   auto fail = [&](int code) {
-    for (void* q : {(void*)EB, (void*)part, (void*)dsc, W64tmp, W->W64, W->W32, W->Wdf, W->W16, W->L32, W->Wtc})
+    for (void* q : {(void*)EB, (void*)part, (void*)dsc, W64tmp, W->W64, W->W32, W->Wdf, W->W16, W->L32, W->Wtc, W->EB32})
       if (q) cudaFreeAsync(q, st);
     delete W;
     return code;
@@ -609,7 +509,14 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
     }
   }
   const size_t nlink = (size_t)g.nblk * LANES * 4 * 9;  // blocked: whole 32-site blocks
-  if (precs & OK_W_LINKS) {
+  const size_t neb = (size_t)g.nblk * LANES * 6 * 9;  // clover fields, blocked
+  if (precs & OK_W_OTF) {
+    e = cudaMallocAsync(&W->EB32, neb * sizeof(cx<float>), st);
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
+    e = cudaMemsetAsync(W->EB32, 0, neb * sizeof(cx<float>), st);
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
+  }
+  if (precs & (OK_W_LINKS | OK_W_OTF)) {
     e = cudaMallocAsync(&W->L32, nlink * sizeof(cx<float>), st);
     if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
     e = cudaMemsetAsync(W->L32, 0, nlink * sizeof(cx<float>), st);
@@ -625,7 +532,8 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
   }
   W->bytes = (W->W64 ? elems * sizeof(cx<double>) : 0) + (W->W32 ? elems * sizeof(cx<float>) : 0) +
              (W->Wdf ? elems * sizeof(cx<dd>) : 0) + (W->W16 ? elems * sizeof(cx<__half>) : 0) +
-             (W->L32 ? nlink * sizeof(cx<float>) : 0) + (W->Wtc ? (size_t)g.V * tc_record_bytes() : 0);
+             (W->L32 ? nlink * sizeof(cx<float>) : 0) + (W->Wtc ? (size_t)g.V * tc_record_bytes() : 0) +
+             (W->EB32 ? neb * sizeof(cx<float>) : 0);
   int nb1 = grid_for(g.V, K1_THREADS);
   e = cudaMallocAsync((void**)&EB, (size_t)g.V * 6 * 9 * sizeof(cx<double>), st);
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
@@ -636,6 +544,12 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
   rc = links_prec == OK_F64 ? run_precompute<double>(W, links, c, st, EB, part, dsc, (cx<double>*)W64tmp)
                             : run_precompute<float>(W, links, c, st, EB, part, dsc, (cx<double>*)W64tmp);
   if (rc != OK_SUCCESS) return fail(rc);
+  if (W->EB32) {
+    eb_blocked_kernel<<<grid_for(54LL * g.V, 256), 256, 0, st>>>(EB, (cx<float>*)W->EB32, g.V);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ECUDA); }
+  }
   if (W->Wtc) {
     rc = launch_tc_build(W, W->W64 ? (const cx<double>*)W->W64 : (const cx<double>*)W64tmp, dsc, st);
     if (rc != OK_SUCCESS) return fail(rc);
