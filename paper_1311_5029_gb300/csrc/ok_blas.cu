@@ -33,6 +33,86 @@ template <> struct Unit<float> {
 
 template <typename R> __device__ __forceinline__ cx<R> scal(dcx z) { return mk<R>((R)z.re, (R)z.im); }
 
+// ---------------------------------------------------------------------------- FP32-pipe grid sums
+// The reductions of the FP32 kernels keep every partial sum as a double-float pair (hi + lo, two
+// floats, about 44 significand bits; ok_internal.cuh): each thread adds its chunk sums into pairs,
+// each block sums its threads' pairs with a fixed shuffle tree, and the last block sums the block
+// partials the same way before the FP64 finalisation.  All of it runs on the FP32 pipes.  FP64
+// arithmetic runs at 1/58 of the FP32 rate on this part; done in FP64, the block trees cost more
+// than streaming the vectors, and the last block's tree kept one SM busy for about 6 us after the
+// others had finished.  The order of every sum is fixed by the launch shape.
+template <typename R> struct RedT { using T = double; };
+template <> struct RedT<float> { using T = dd; };
+__device__ __forceinline__ void red_add(double& a, double c) { a += c; }
+__device__ __forceinline__ void red_add(dd& a, float c) { a = a + dd(c, 0.f); }
+__device__ __forceinline__ dd shfl_xor_dd(dd a, int o) {
+  return dd(__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o));
+}
+
+template <int NP, int THREADS>
+__device__ __forceinline__ void block_sums_dd(dd (&v)[NP], dd (*sh)[THREADS / 32]) {
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    dd x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = x + shfl_xor_dd(x, o);
+    if ((threadIdx.x & 31) == 0) sh[k][threadIdx.x >> 5] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      dd x = sh[k][0];
+      for (int w = 1; w < THREADS / 32; ++w) x = x + sh[k][w];
+      v[k] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// grid_reduce (ok_reduce.cuh) in double-float: block partials stored as doubles (hi + lo, exact),
+// the last block sums them and finalises.
+template <int NP, int THREADS>
+__device__ __forceinline__ void grid_reduce_dd(dd (&v)[NP], const RedArgs& ra, unsigned* ticket) {
+  __shared__ dd sh[NP][THREADS / 32];
+  __shared__ int last;
+  block_sums_dd<NP, THREADS>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) ra.part[(size_t)blockIdx.x * NP + k] = (double)v[k];
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  dd w[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) w[k] = dd(0.f, 0.f);
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += THREADS)
+#pragma unroll
+    for (int k = 0; k < NP; ++k) w[k] = w[k] + dd(__ldcg(ra.part + (size_t)b * NP + k));
+  block_sums_dd<NP, THREADS>(w, sh);
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
+    double tot[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < NP && k < 4; ++k) tot[k] = (double)w[k];
+    if (ra.out) {
+#pragma unroll
+      for (int k = 0; k < NP; ++k) ra.out[k] = tot[k];
+    }
+    finalise(ra.st, ra.fin, tot);
+  }
+}
+
+// The grid reduction of the precision R's kernels.
+template <typename R, int NP>
+__device__ __forceinline__ void grid_reduce_r(typename RedT<R>::T (&v)[NP], const RedArgs& ra, unsigned* ticket) {
+  if constexpr (sizeof(R) == 4) grid_reduce_dd<NP, BLAS_THREADS>(v, ra, ticket);
+  else grid_reduce<NP, BLAS_THREADS>(v, ra, ticket);
+}
+
 #define OK_GRID_STRIDE(i, n) for (long long i = blockIdx.x * (long long)BLAS_THREADS + threadIdx.x; i < (n); i += (long long)gridDim.x * BLAS_THREADS)
 
 // The reducing kernels sum RED_CHUNK units per thread in the vectors' own precision and add each
@@ -88,7 +168,7 @@ __global__ void __launch_bounds__(BLAS_THREADS) update_xr_kernel(typename Unit<R
   if (st->halt) return;
   using U = Unit<R>;
   const cx<R> al = scal<R>(st->alpha), om = scal<R>(st->omega);
-  double red[3] = {0.0, 0.0, 0.0};
+  typename RedT<R>::T red[3] = {0, 0, 0};
   OK_CHUNK_STRIDE(i0, nu) {
     cx<R> d = mk<R>(0, 0);
     R n2 = 0;
@@ -110,11 +190,11 @@ __global__ void __launch_bounds__(BLAS_THREADS) update_xr_kernel(typename Unit<R
       x[i] = U::put(xv);
       r[i] = U::put(sv);
     }
-    red[0] += d.re;
-    red[1] += d.im;
-    red[2] += n2;
+    red_add(red[0], d.re);
+    red_add(red[1], d.im);
+    red_add(red[2], n2);
   }
-  grid_reduce<3, BLAS_THREADS>(red, ra, &st->ticket[2]);
+  grid_reduce_r<R, 3>(red, ra, &st->ticket[2]);
 }
 
 // p = r + beta (p - omega v)
@@ -149,7 +229,7 @@ __global__ void __launch_bounds__(BLAS_THREADS) dots_kernel(const typename Unit<
                                                             SolverState* __restrict__ st, RedArgs ra, unsigned* ticket) {
   if (st->halt) return;
   using U = Unit<R>;
-  double red[3] = {0.0, 0.0, 0.0};
+  typename RedT<R>::T red[3] = {0, 0, 0};
   OK_CHUNK_STRIDE(i0, nu) {
     cx<R> d = mk<R>(0, 0);
     R n2 = 0;
@@ -163,15 +243,15 @@ __global__ void __launch_bounds__(BLAS_THREADS) dots_kernel(const typename Unit<
         if (OMEGA) n2 += av[k].re * av[k].re + av[k].im * av[k].im;
       }
     }
-    red[0] += d.re;
-    red[1] += d.im;
-    red[2] += n2;
+    red_add(red[0], d.re);
+    red_add(red[1], d.im);
+    red_add(red[2], n2);
   }
   if (OMEGA) {
-    grid_reduce<3, BLAS_THREADS>(red, ra, ticket);
+    grid_reduce_r<R, 3>(red, ra, ticket);
   } else {
-    double v2[2] = {red[0], red[1]};
-    grid_reduce<2, BLAS_THREADS>(v2, ra, ticket);
+    typename RedT<R>::T v2[2] = {red[0], red[1]};
+    grid_reduce_r<R, 2>(v2, ra, ticket);
   }
 }
 
@@ -182,7 +262,7 @@ __global__ void __launch_bounds__(BLAS_THREADS) restart_kernel(const typename Un
                                                                typename Unit<R>::T* __restrict__ p, long long nu,
                                                                SolverState* __restrict__ st, RedArgs ra) {
   using U = Unit<R>;
-  double red[1] = {0.0};
+  typename RedT<R>::T red[1] = {0};
   OK_CHUNK_STRIDE(i0, nu) {
     R n2 = 0;
     OK_CHUNK_UNITS(i, i0, nu) {
@@ -194,9 +274,9 @@ __global__ void __launch_bounds__(BLAS_THREADS) restart_kernel(const typename Un
 #pragma unroll
       for (int k = 0; k < U::NC; ++k) n2 += a[k].re * a[k].re + a[k].im * a[k].im;
     }
-    red[0] += n2;
+    red_add(red[0], n2);
   }
-  grid_reduce<1, BLAS_THREADS>(red, ra, &st->ticket[3]);
+  grid_reduce_r<R, 1>(red, ra, &st->ticket[3]);
 }
 
 // Mixed precision: r32 = (float) r64; RESTART: rhat = p = r32 and FIN_RESTART on <r, r>;
