@@ -376,7 +376,7 @@ int blas_blocks(long long units) {
 // block's partial ends in a fence and an atomic on one completion counter, and at a full wave
 // (up to 8 x 152 blocks) those serialised atomics cost more than the few extra loads in flight.
 #ifndef OK_RED_BLOCKS_PER_SM
-#define OK_RED_BLOCKS_PER_SM 2
+#define OK_RED_BLOCKS_PER_SM 4
 #endif
 template <typename K>
 static int wave_blocks(K kern, long long units, bool reduces = false) {
