@@ -28,10 +28,10 @@
 // 2 x 4, spatial 6 x 2, two-hop 6 x 2, diagonal 12 x 2.
 //
 // Field layout (the solve's iteration vectors).  Unit (site, b, r, c) = (h_b spin 0, h_b spin 1) at
-// colour c of right-hand side r, at unit index ((site * 2 + b) * nrhs + r) * 3 + c: 16 bytes in
-// FP32, 8 bytes in FP16.  The apply reads FP16 units (the products' A operands as they are: one
-// 8-byte load per lane and neighbour tile out of one contiguous record) and writes FP32 units,
-// which are exactly the accumulators a lane holds after the products.
+// colour c of right-hand side r, at unit index ((site * 2 + b) * nrhs + r) * 3 + c, 16 bytes in
+// FP32.  The apply writes these units: they are exactly the accumulators a lane holds after the
+// products.  It reads FP16 copies in the tile layout of in16_index below (the A operands as the
+// products take them, one 16-byte load per lane and neighbour projection).
 //
 // Range of the FP16 inputs.  A residual shrinks by many orders of magnitude during a solve, below
 // the FP16 range, so each right-hand side's FP16 input carries a power-of-two scale sigma_r (exact
