@@ -162,6 +162,22 @@ __device__ __forceinline__ void store_mat(const WOut& o, int site, int m, const 
   }
 }
 
+// The same stores from a double-float result (the FP32-pipe precompute, used when no native FP64
+// copy is kept): the double-float copy takes the pairs as they are, the FP32 and FP16 copies the
+// rounded high parts.
+__device__ __forceinline__ void store_mat(const WOut& o, int site, int m, const M3<dd>& a) {
+  size_t blk = (size_t)(site >> 5);
+  int lane = site & 31;
+  size_t base = (blk * NMAT + m) * 9 * LANES + lane;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    if (o.Wdf) o.Wdf[base + (size_t)e * LANES] = a.e[e];
+    const float re = a.e[e].re.hi + a.e[e].re.lo, im = a.e[e].im.hi + a.e[e].im.lo;
+    if (o.W32) o.W32[base + (size_t)e * LANES] = mk<float>(re, im);
+    if (o.W16) o.W16[base + (size_t)e * LANES] = mk<__half>(__float2half_rn(re), __float2half_rn(im));
+  }
+}
+
 constexpr int K2_THREADS = 64;
 
 // The inputs of the W formulas in the precompute: canonical links (FP64 or FP32) and the FP64 clover
@@ -174,45 +190,70 @@ struct CanonInputs {
   __device__ __forceinline__ M3<double> F(int site, int k) const { return load_eb(EB, site, k); }
 };
 
+// The inputs as double-float pairs (converted once per precompute): the W formulas then run on the
+// FP32 pipes, which GB300 executes 58 times faster than its FP64 pipe, with errors of about 1e-13
+// relative instead of FP64 rounding.
+struct DDInputs {
+  const cx<dd>* __restrict__ links;  // [V][4][9]
+  const cx<dd>* __restrict__ EB;     // [V][6][9]
+  __device__ __forceinline__ static M3<dd> get(const cx<dd>* __restrict__ p) {
+    M3<dd> m;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(p) + e);
+      m.e[e] = mk(dd(v.x, v.y), dd(v.z, v.w));
+    }
+    return m;
+  }
+  __device__ __forceinline__ M3<dd> U(int site, int mu) const { return get(links + ((size_t)site * 4 + mu) * 9); }
+  __device__ __forceinline__ M3<dd> F(int site, int k) const { return get(EB + ((size_t)site * 6 + k) * 9); }
+};
+
+// Complex FP64 or FP32 values -> double-float pairs (hi = RN(d), lo = RN(d - hi)).
+template <typename T>
+__global__ void to_dd_kernel(const cx<T>* __restrict__ in, cx<dd>* __restrict__ out, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const cx<T> v = in[i];
+  out[i] = mk(dd((double)v.re), dd((double)v.im));
+}
+
 // part 0: W^0 and W^+_4; parts 1..3: W^+_i for i = part - 1; part 4: W^{++}_ii, W^{++}_ij, W^{+-}_ij
-// (the formulas are those of ok_wform.cuh, in FP64).
-template <typename LT>
-__global__ void __launch_bounds__(K2_THREADS) w_kernel(const cx<LT>* __restrict__ U,
-                                                       const cx<double>* __restrict__ EB, Geom g,
-                                                       ok_coeffs c, const WScalars* __restrict__ scp,
+// (the formulas of ok_wform.cuh, in precision R: FP64 from CanonInputs, double-float from DDInputs).
+template <typename R, class In>
+__global__ void __launch_bounds__(K2_THREADS) w_kernel(In in, Geom g, ok_coeffs c, const WScalars* __restrict__ scp,
                                                        WOut o, int part) {
   int s = blockIdx.x * K2_THREADS + threadIdx.x;
   if (s >= g.V) return;
   const double u0 = scp->u0;
   const Site p = site_coords(s, g);
-  const CanonInputs<LT> in{U, EB};
   if (part == 0) {
-    M3<double> yp[3], ym[3], t[3], uh;
-    wform::onsite<double>(in, s, c, u0, yp, ym);
+    M3<R> yp[3], ym[3], t[3], uh;
+    wform::onsite<R>(in, s, c, u0, yp, ym);
     for (int j = 0; j < 3; ++j) {
       store_mat(o, s, M_Y0P + j, yp[j]);
       store_mat(o, s, M_Y0M + j, ym[j]);
     }
-    wform::temporal<double>(in, p, g, s, c, u0, uh, t);
+    wform::temporal<R>(in, p, g, s, c, u0, uh, t);
     store_mat(o, s, M_UT, uh);
     for (int j = 0; j < 3; ++j) store_mat(o, s, M_ST + j, t[j]);
     return;
   }
   if (part >= 1 && part <= 3) {
     const int i = part - 1;
-    M3<double> q[8];
-    wform::spatial<double>(in, p, g, s, i, c, u0, q);
+    M3<R> q[8];
+    wform::spatial<R>(in, p, g, s, i, c, u0, q);
     for (int k = 0; k < 8; ++k) store_mat(o, s, M_WP + 8 * i + k, q[k]);
     return;
   }
   // part 4: two-hop colour matrices
-  for (int i = 0; i < 3; ++i) store_mat(o, s, M_VII + i, wform::twohop<double>(in, p, g, s, i));
+  for (int i = 0; i < 3; ++i) store_mat(o, s, M_VII + i, wform::twohop<R>(in, p, g, s, i));
   int pr = 0;
   for (int i = 0; i < 3; ++i) {
     for (int j = i + 1; j < 3; ++j, ++pr) {
-      M3<double> v, x;
-      wform::diag_v<double>(in, p, g, s, i, j, c, u0, v);
-      wform::diag_x<double>(in, p, g, s, i, j, c, u0, x);
+      M3<R> v, x;
+      wform::diag_v<R>(in, p, g, s, i, j, c, u0, v);
+      wform::diag_x<R>(in, p, g, s, i, j, c, u0, x);
       store_mat(o, s, M_VIJ + pr, v);
       store_mat(o, s, M_XIJ + pr, x);
     }
@@ -389,14 +430,50 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
   WOut o{W->W64 ? (cx<double>*)W->W64 : W64tmp, (cx<float>*)W->W32, (cx<dd>*)W->Wdf, (cx<__half>*)W->W16};
   int nb2 = grid_for(g.V, K2_THREADS);
   const bool any_w = o.W64 || o.W32 || o.Wdf || o.W16;  // (a handle for the on-the-fly apply stores none)
-  for (int part_id = 0; any_w && part_id < 5; ++part_id) {
-    {
+  if (!any_w) return OK_SUCCESS;
+  if (o.W64) {
+    // a native FP64 copy (kept, or read by the tensor-core build): the formulas in FP64
+    const CanonInputs<LT> in{U, EB};
+    for (int part_id = 0; part_id < 5; ++part_id) {
+      {
+        TraceScope ts("w_build", st);
+        w_kernel<double><<<nb2, K2_THREADS, 0, st>>>(in, g, *c, dsc, o, part_id);
+      }
+      OK_LAUNCH_CHECK();
+    }
+    return OK_SUCCESS;
+  }
+  // otherwise in double-float on the FP32 pipes, from double-float copies of the links and fields
+  cx<dd>* ldd = nullptr;
+  cx<dd>* ebdd = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&ldd, (size_t)g.V * 36 * sizeof(cx<dd>), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&ebdd, (size_t)g.V * 54 * sizeof(cx<dd>), st);
+  if (e != cudaSuccess) {
+    if (ldd) cudaFreeAsync(ldd, st);
+    set_cuda_error(e);
+    return OK_ENOMEM;
+  }
+  int rc = OK_SUCCESS;
+  {
     TraceScope ts("w_build", st);
-    w_kernel<LT><<<nb2, K2_THREADS, 0, st>>>(U, EB, g, *c, dsc, o, part_id);
+    to_dd_kernel<LT><<<grid_for(36LL * g.V, 256), 256, 0, st>>>(U, ldd, 36LL * g.V);
+    to_dd_kernel<double><<<grid_for(54LL * g.V, 256), 256, 0, st>>>(EB, ebdd, 54LL * g.V);
+    count_launch();
+    count_launch();
+    const DDInputs in{ldd, ebdd};
+    for (int part_id = 0; part_id < 5; ++part_id) {
+      w_kernel<dd><<<nb2, K2_THREADS, 0, st>>>(in, g, *c, dsc, o, part_id);
+      count_launch();
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      rc = OK_ECUDA;
+    }
   }
-    OK_LAUNCH_CHECK();
-  }
-  return OK_SUCCESS;
+  cudaFreeAsync(ldd, st);
+  cudaFreeAsync(ebdd, st);
+  return rc;
 }
 
 // Clover fields (FP64, [V][6][9]) -> the FP32 copy of an OK_W_OTF handle, site-blocked like W:
