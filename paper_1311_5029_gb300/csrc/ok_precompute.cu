@@ -60,55 +60,90 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
+// The inputs of the W formulas in the precompute: canonical links (FP64 or FP32) and the FP64 clover
+// fields of clover_kernel.
+template <typename LT>
+struct CanonInputs {
+  const cx<LT>* __restrict__ links;
+  const cx<double>* __restrict__ EB;
+  __device__ __forceinline__ M3<double> U(int site, int mu) const { return load_link(links, site, mu); }
+  __device__ __forceinline__ M3<double> F(int site, int k) const { return load_eb(EB, site, k); }
+};
+
+// The inputs as double-float pairs (converted once per precompute): the W formulas then run on the
+// FP32 pipes, which GB300 executes 58 times faster than its FP64 pipe, with errors of about 1e-13
+// relative instead of FP64 rounding.
+struct DDInputs {
+  const cx<dd>* __restrict__ links;  // [V][4][9]
+  const cx<dd>* __restrict__ EB;     // [V][6][9]
+  __device__ __forceinline__ static M3<dd> get(const cx<dd>* __restrict__ p) {
+    M3<dd> m;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(p) + e);
+      m.e[e] = mk(dd(v.x, v.y), dd(v.z, v.w));
+    }
+    return m;
+  }
+  __device__ __forceinline__ M3<dd> U(int site, int mu) const { return get(links + ((size_t)site * 4 + mu) * 9); }
+  __device__ __forceinline__ M3<dd> F(int site, int k) const { return get(EB + ((size_t)site * 6 + k) * 9); }
+};
+
+// Complex FP64 or FP32 values -> double-float pairs (hi = RN(d), lo = RN(d - hi)).
+template <typename T>
+__global__ void to_dd_kernel(const cx<T>* __restrict__ in, cx<dd>* __restrict__ out, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const cx<T> v = in[i];
+  out[i] = mk(dd((double)v.re), dd((double)v.im));
+}
+
 // ---------------------------------------------------------------------------- K1: clover + plaquette
 // F_{mu nu} = (Q - Q^dagger) / 8 with Q the four plaquette leaves around x traversed mu-then-nu;
 // E_i = F_{t i}, B_i = eps_ijk F_jk / 2.  The plaquette leaf U_mu(x) U_nu(x+mu) U_mu^dag(x+nu)
 // U_nu^dag(x) also feeds the mean plaquette.
 constexpr int K1_THREADS = 128;
 
-template <typename LT>
-__global__ void __launch_bounds__(K1_THREADS) clover_kernel(const cx<LT>* __restrict__ U, Geom g,
-                                                            cx<double>* __restrict__ EB,
+// In precision R from the input accessor `in` (U(site, mu)); the fields are stored and the
+// plaquette summed in FP64.
+template <typename R, class In>
+__global__ void __launch_bounds__(K1_THREADS) clover_kernel(In in, Geom g, cx<double>* __restrict__ EB,
                                                             double* __restrict__ plaq_part) {
   __shared__ double sh[K1_THREADS / 32];
   int s = blockIdx.x * K1_THREADS + threadIdx.x;
   double retr = 0.0;
   if (s < g.V) {
     Site p = site_coords(s, g);
-    M3<double> F[4][4];
+    cx<double>* out = EB + (size_t)s * 6 * 9;
     for (int mu = 0; mu < 4; ++mu) {
       for (int nu = mu + 1; nu < 4; ++nu) {
-        M3<double> Umx = load_link(U, s, mu), Unx = load_link(U, s, nu);
+        M3<R> Umx = in.U(s, mu), Unx = in.U(s, nu);
         // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-        M3<double> l1 = m_mul(m_mul(Umx, load_link(U, nbr_dir(p, g, mu, 1), nu)),
-                              m_mul(m_dag(load_link(U, nbr_dir(p, g, nu, 1), mu)), m_dag(Unx)));
+        M3<R> l1 = m_mul(m_mul(Umx, in.U(nbr_dir(p, g, mu, 1), nu)),
+                              m_mul(m_dag(in.U(nbr_dir(p, g, nu, 1), mu)), m_dag(Unx)));
         // leaf 2: U_nu(x) U_mu(x+nu-mu)^dag U_nu(x-mu)^dag U_mu(x-mu)
-        M3<double> l2 = m_mul(m_mul(Unx, m_dag(load_link(U, nbr_dir(p, g, nu, 1, mu, -1), mu))),
-                              m_mul(m_dag(load_link(U, nbr_dir(p, g, mu, -1), nu)),
-                                    load_link(U, nbr_dir(p, g, mu, -1), mu)));
+        M3<R> l2 = m_mul(m_mul(Unx, m_dag(in.U(nbr_dir(p, g, nu, 1, mu, -1), mu))),
+                              m_mul(m_dag(in.U(nbr_dir(p, g, mu, -1), nu)),
+                                    in.U(nbr_dir(p, g, mu, -1), mu)));
         // leaf 3: U_mu(x-mu)^dag U_nu(x-mu-nu)^dag U_mu(x-mu-nu) U_nu(x-nu)
-        M3<double> l3 = m_mul(m_mul(m_dag(load_link(U, nbr_dir(p, g, mu, -1), mu)),
-                                    m_dag(load_link(U, nbr_dir(p, g, mu, -1, nu, -1), nu))),
-                              m_mul(load_link(U, nbr_dir(p, g, mu, -1, nu, -1), mu),
-                                    load_link(U, nbr_dir(p, g, nu, -1), nu)));
+        M3<R> l3 = m_mul(m_mul(m_dag(in.U(nbr_dir(p, g, mu, -1), mu)),
+                                    m_dag(in.U(nbr_dir(p, g, mu, -1, nu, -1), nu))),
+                              m_mul(in.U(nbr_dir(p, g, mu, -1, nu, -1), mu),
+                                    in.U(nbr_dir(p, g, nu, -1), nu)));
         // leaf 4: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^dag
-        M3<double> l4 = m_mul(m_mul(m_dag(load_link(U, nbr_dir(p, g, nu, -1), nu)),
-                                    load_link(U, nbr_dir(p, g, nu, -1), mu)),
-                              m_mul(load_link(U, nbr_dir(p, g, nu, -1, mu, 1), nu), m_dag(Umx)));
-        retr += l1.e[0].re + l1.e[4].re + l1.e[8].re;
-        M3<double> Q = m_add(m_add(l1, l2), m_add(l3, l4));
-        M3<double> f = m_rscale(0.125, m_sub(Q, m_dag(Q)));
-        F[mu][nu] = f;
-        F[nu][mu] = m_rscale(-1.0, f);
-      }
-    }
-    cx<double>* out = EB + (size_t)s * 6 * 9;
-    for (int i = 0; i < 3; ++i) {
-      const M3<double>& E = F[3][i];
-      const M3<double>& B = F[(i + 1) % 3][(i + 2) % 3];
-      for (int e = 0; e < 9; ++e) {
-        out[i * 9 + e] = E.e[e];
-        out[(3 + i) * 9 + e] = B.e[e];
+        M3<R> l4 = m_mul(m_mul(m_dag(in.U(nbr_dir(p, g, nu, -1), nu)),
+                                    in.U(nbr_dir(p, g, nu, -1), mu)),
+                              m_mul(in.U(nbr_dir(p, g, nu, -1, mu, 1), nu), m_dag(Umx)));
+        retr += (double)l1.e[0].re + (double)l1.e[4].re + (double)l1.e[8].re;
+        M3<R> Q = m_add(m_add(l1, l2), m_add(l3, l4));
+        const M3<R> f = m_rscale((R)0.125, m_sub(Q, m_dag(Q)));
+        // F_{mu nu} is E_i = F_{t i} = -F_{i t} (nu = t) or B_k = F_{(k+1)(k+2)} (indices mod 3)
+        int slot;
+        double sg;
+        if (nu == 3) { slot = mu; sg = -1.0; }
+        else { const int k = 3 - mu - nu; slot = 3 + k; sg = (nu == (mu + 1) % 3) ? 1.0 : -1.0; }
+        for (int e = 0; e < 9; ++e)
+          out[slot * 9 + e] = mk(sg * (double)f.e[e].re, sg * (double)f.e[e].im);
       }
     }
   }
@@ -180,43 +215,6 @@ __device__ __forceinline__ void store_mat(const WOut& o, int site, int m, const 
 
 constexpr int K2_THREADS = 64;
 
-// The inputs of the W formulas in the precompute: canonical links (FP64 or FP32) and the FP64 clover
-// fields of clover_kernel.
-template <typename LT>
-struct CanonInputs {
-  const cx<LT>* __restrict__ links;
-  const cx<double>* __restrict__ EB;
-  __device__ __forceinline__ M3<double> U(int site, int mu) const { return load_link(links, site, mu); }
-  __device__ __forceinline__ M3<double> F(int site, int k) const { return load_eb(EB, site, k); }
-};
-
-// The inputs as double-float pairs (converted once per precompute): the W formulas then run on the
-// FP32 pipes, which GB300 executes 58 times faster than its FP64 pipe, with errors of about 1e-13
-// relative instead of FP64 rounding.
-struct DDInputs {
-  const cx<dd>* __restrict__ links;  // [V][4][9]
-  const cx<dd>* __restrict__ EB;     // [V][6][9]
-  __device__ __forceinline__ static M3<dd> get(const cx<dd>* __restrict__ p) {
-    M3<dd> m;
-#pragma unroll
-    for (int e = 0; e < 9; ++e) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(p) + e);
-      m.e[e] = mk(dd(v.x, v.y), dd(v.z, v.w));
-    }
-    return m;
-  }
-  __device__ __forceinline__ M3<dd> U(int site, int mu) const { return get(links + ((size_t)site * 4 + mu) * 9); }
-  __device__ __forceinline__ M3<dd> F(int site, int k) const { return get(EB + ((size_t)site * 6 + k) * 9); }
-};
-
-// Complex FP64 or FP32 values -> double-float pairs (hi = RN(d), lo = RN(d - hi)).
-template <typename T>
-__global__ void to_dd_kernel(const cx<T>* __restrict__ in, cx<dd>* __restrict__ out, long long n) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const cx<T> v = in[i];
-  out[i] = mk(dd((double)v.re), dd((double)v.im));
-}
 
 // part 0: W^0 and W^+_4; parts 1..3: W^+_i for i = part - 1; part 4: W^{++}_ii, W^{++}_ij, W^{+-}_ij
 // (the formulas of ok_wform.cuh, in precision R: FP64 from CanonInputs, double-float from DDInputs).
@@ -417,63 +415,66 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
   const Geom& g = W->g;
   const cx<LT>* U = (const cx<LT>*)links;
   int nb1 = grid_for(g.V, K1_THREADS);
+  int nb2 = grid_for(g.V, K2_THREADS);
+  WOut o{W->W64 ? (cx<double>*)W->W64 : W64tmp, (cx<float>*)W->W32, (cx<dd>*)W->Wdf, (cx<__half>*)W->W16};
+  const bool any_w = o.W64 || o.W32 || o.Wdf || o.W16;  // (a handle for the on-the-fly apply stores none)
+  // A native FP64 copy (kept, or read by the tensor-core build) is computed in FP64; otherwise W is
+  // computed in double-float on the FP32 pipes, from double-float copies of the links and fields.
+  const bool fp64 = o.W64 != nullptr;
+  cx<dd>* ldd = nullptr;
+  cx<dd>* ebdd = nullptr;
+  auto release = [&]() {
+    if (ldd) cudaFreeAsync(ldd, st);
+    if (ebdd) cudaFreeAsync(ebdd, st);
+  };
+  if (!fp64 && any_w) {
+    cudaError_t e = cudaMallocAsync((void**)&ldd, (size_t)g.V * 36 * sizeof(cx<dd>), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&ebdd, (size_t)g.V * 54 * sizeof(cx<dd>), st);
+    if (e != cudaSuccess) {
+      release();
+      set_cuda_error(e);
+      return OK_ENOMEM;
+    }
+  }
   {
     TraceScope ts("clover", st);
-    clover_kernel<LT><<<nb1, K1_THREADS, 0, st>>>(U, g, EB, part);
+    // (in FP64 always: in double-float it took as long, 2.2 ms at 16^3 x 32; it is bound by the
+    // latency of its link gathers at 8 warps per SM, not by the FP64 pipe)
+    clover_kernel<double><<<nb1, K1_THREADS, 0, st>>>(CanonInputs<LT>{U, EB}, g, EB, part);
   }
-  OK_LAUNCH_CHECK();
+  count_launch();
   {
     TraceScope ts("plaquette_u0", st);
     scalars_kernel<<<1, 256, 0, st>>>(part, nb1, g, *c, dsc);
   }
-  OK_LAUNCH_CHECK();
-  WOut o{W->W64 ? (cx<double>*)W->W64 : W64tmp, (cx<float>*)W->W32, (cx<dd>*)W->Wdf, (cx<__half>*)W->W16};
-  int nb2 = grid_for(g.V, K2_THREADS);
-  const bool any_w = o.W64 || o.W32 || o.Wdf || o.W16;  // (a handle for the on-the-fly apply stores none)
-  if (!any_w) return OK_SUCCESS;
-  if (o.W64) {
-    // a native FP64 copy (kept, or read by the tensor-core build): the formulas in FP64
-    const CanonInputs<LT> in{U, EB};
-    for (int part_id = 0; part_id < 5; ++part_id) {
-      {
-        TraceScope ts("w_build", st);
-        w_kernel<double><<<nb2, K2_THREADS, 0, st>>>(in, g, *c, dsc, o, part_id);
-      }
-      OK_LAUNCH_CHECK();
-    }
-    return OK_SUCCESS;
-  }
-  // otherwise in double-float on the FP32 pipes, from double-float copies of the links and fields
-  cx<dd>* ldd = nullptr;
-  cx<dd>* ebdd = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&ldd, (size_t)g.V * 36 * sizeof(cx<dd>), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&ebdd, (size_t)g.V * 54 * sizeof(cx<dd>), st);
-  if (e != cudaSuccess) {
-    if (ldd) cudaFreeAsync(ldd, st);
-    set_cuda_error(e);
-    return OK_ENOMEM;
-  }
-  int rc = OK_SUCCESS;
-  {
+  count_launch();
+  if (any_w) {
     TraceScope ts("w_build", st);
-    to_dd_kernel<LT><<<grid_for(36LL * g.V, 256), 256, 0, st>>>(U, ldd, 36LL * g.V);
-    to_dd_kernel<double><<<grid_for(54LL * g.V, 256), 256, 0, st>>>(EB, ebdd, 54LL * g.V);
-    count_launch();
-    count_launch();
-    const DDInputs in{ldd, ebdd};
-    for (int part_id = 0; part_id < 5; ++part_id) {
-      w_kernel<dd><<<nb2, K2_THREADS, 0, st>>>(in, g, *c, dsc, o, part_id);
+    if (fp64) {
+      const CanonInputs<LT> in{U, EB};
+      for (int part_id = 0; part_id < 5; ++part_id) {
+        w_kernel<double><<<nb2, K2_THREADS, 0, st>>>(in, g, *c, dsc, o, part_id);
+        count_launch();
+      }
+    } else {
+      to_dd_kernel<LT><<<grid_for(36LL * g.V, 256), 256, 0, st>>>(U, ldd, 36LL * g.V);
+      to_dd_kernel<double><<<grid_for(54LL * g.V, 256), 256, 0, st>>>(EB, ebdd, 54LL * g.V);
       count_launch();
-    }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      set_cuda_error(e);
-      rc = OK_ECUDA;
+      count_launch();
+      const DDInputs in{ldd, ebdd};
+      for (int part_id = 0; part_id < 5; ++part_id) {
+        w_kernel<dd><<<nb2, K2_THREADS, 0, st>>>(in, g, *c, dsc, o, part_id);
+        count_launch();
+      }
     }
   }
-  cudaFreeAsync(ldd, st);
-  cudaFreeAsync(ebdd, st);
-  return rc;
+  const cudaError_t e = cudaGetLastError();
+  release();
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return OK_ECUDA;
+  }
+  return OK_SUCCESS;
 }
 
 // Clover fields (FP64, [V][6][9]) -> the FP32 copy of an OK_W_OTF handle, site-blocked like W:
