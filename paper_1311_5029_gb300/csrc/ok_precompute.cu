@@ -104,51 +104,47 @@ __global__ void to_dd_kernel(const cx<T>* __restrict__ in, cx<dd>* __restrict__ 
 // U_nu^dag(x) also feeds the mean plaquette.
 constexpr int K1_THREADS = 128;
 
-// In precision R from the input accessor `in` (U(site, mu)); the fields are stored and the
-// plaquette summed in FP64.
+// One thread per (site, plane): blockIdx.y is the plane (mu, nu), mu < nu, in the order (0,1),
+// (0,2), (0,3), (1,2), (1,3), (2,3).  In precision R from the input accessor `in` (U(site, mu)); the
+// field is stored in FP64 in its E or B slot, and the plaquette leaf summed in FP64 into the
+// partial of block (blockIdx.y, blockIdx.x).
 template <typename R, class In>
 __global__ void __launch_bounds__(K1_THREADS) clover_kernel(In in, Geom g, cx<double>* __restrict__ EB,
                                                             double* __restrict__ plaq_part) {
   __shared__ double sh[K1_THREADS / 32];
-  int s = blockIdx.x * K1_THREADS + threadIdx.x;
+  const int s = blockIdx.x * K1_THREADS + threadIdx.x;
+  const int pl = blockIdx.y;
+  const int mu = pl < 3 ? 0 : pl < 5 ? 1 : 2;
+  const int nu = pl < 3 ? pl + 1 : pl < 5 ? pl - 1 : 3;
   double retr = 0.0;
   if (s < g.V) {
-    Site p = site_coords(s, g);
-    cx<double>* out = EB + (size_t)s * 6 * 9;
-    for (int mu = 0; mu < 4; ++mu) {
-      for (int nu = mu + 1; nu < 4; ++nu) {
-        M3<R> Umx = in.U(s, mu), Unx = in.U(s, nu);
-        // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-        M3<R> l1 = m_mul(m_mul(Umx, in.U(nbr_dir(p, g, mu, 1), nu)),
-                              m_mul(m_dag(in.U(nbr_dir(p, g, nu, 1), mu)), m_dag(Unx)));
-        // leaf 2: U_nu(x) U_mu(x+nu-mu)^dag U_nu(x-mu)^dag U_mu(x-mu)
-        M3<R> l2 = m_mul(m_mul(Unx, m_dag(in.U(nbr_dir(p, g, nu, 1, mu, -1), mu))),
-                              m_mul(m_dag(in.U(nbr_dir(p, g, mu, -1), nu)),
-                                    in.U(nbr_dir(p, g, mu, -1), mu)));
-        // leaf 3: U_mu(x-mu)^dag U_nu(x-mu-nu)^dag U_mu(x-mu-nu) U_nu(x-nu)
-        M3<R> l3 = m_mul(m_mul(m_dag(in.U(nbr_dir(p, g, mu, -1), mu)),
-                                    m_dag(in.U(nbr_dir(p, g, mu, -1, nu, -1), nu))),
-                              m_mul(in.U(nbr_dir(p, g, mu, -1, nu, -1), mu),
-                                    in.U(nbr_dir(p, g, nu, -1), nu)));
-        // leaf 4: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^dag
-        M3<R> l4 = m_mul(m_mul(m_dag(in.U(nbr_dir(p, g, nu, -1), nu)),
-                                    in.U(nbr_dir(p, g, nu, -1), mu)),
-                              m_mul(in.U(nbr_dir(p, g, nu, -1, mu, 1), nu), m_dag(Umx)));
-        retr += (double)l1.e[0].re + (double)l1.e[4].re + (double)l1.e[8].re;
-        M3<R> Q = m_add(m_add(l1, l2), m_add(l3, l4));
-        const M3<R> f = m_rscale((R)0.125, m_sub(Q, m_dag(Q)));
-        // F_{mu nu} is E_i = F_{t i} = -F_{i t} (nu = t) or B_k = F_{(k+1)(k+2)} (indices mod 3)
-        int slot;
-        double sg;
-        if (nu == 3) { slot = mu; sg = -1.0; }
-        else { const int k = 3 - mu - nu; slot = 3 + k; sg = (nu == (mu + 1) % 3) ? 1.0 : -1.0; }
-        for (int e = 0; e < 9; ++e)
-          out[slot * 9 + e] = mk(sg * (double)f.e[e].re, sg * (double)f.e[e].im);
-      }
-    }
+    const Site p = site_coords(s, g);
+    const M3<R> Umx = in.U(s, mu), Unx = in.U(s, nu);
+    // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+    const M3<R> l1 = m_mul(m_mul(Umx, in.U(nbr_dir(p, g, mu, 1), nu)),
+                           m_mul(m_dag(in.U(nbr_dir(p, g, nu, 1), mu)), m_dag(Unx)));
+    retr = (double)l1.e[0].re + (double)l1.e[4].re + (double)l1.e[8].re;
+    M3<R> Q = l1;
+    // leaf 2: U_nu(x) U_mu(x+nu-mu)^dag U_nu(x-mu)^dag U_mu(x-mu)
+    Q = m_add(Q, m_mul(m_mul(Unx, m_dag(in.U(nbr_dir(p, g, nu, 1, mu, -1), mu))),
+                       m_mul(m_dag(in.U(nbr_dir(p, g, mu, -1), nu)), in.U(nbr_dir(p, g, mu, -1), mu))));
+    // leaf 3: U_mu(x-mu)^dag U_nu(x-mu-nu)^dag U_mu(x-mu-nu) U_nu(x-nu)
+    Q = m_add(Q, m_mul(m_mul(m_dag(in.U(nbr_dir(p, g, mu, -1), mu)), m_dag(in.U(nbr_dir(p, g, mu, -1, nu, -1), nu))),
+                       m_mul(in.U(nbr_dir(p, g, mu, -1, nu, -1), mu), in.U(nbr_dir(p, g, nu, -1), nu))));
+    // leaf 4: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^dag
+    Q = m_add(Q, m_mul(m_mul(m_dag(in.U(nbr_dir(p, g, nu, -1), nu)), in.U(nbr_dir(p, g, nu, -1), mu)),
+                       m_mul(in.U(nbr_dir(p, g, nu, -1, mu, 1), nu), m_dag(Umx))));
+    const M3<R> f = m_rscale((R)0.125, m_sub(Q, m_dag(Q)));
+    // F_{mu nu} is E_i = F_{t i} = -F_{i t} (nu = t) or B_k = F_{(k+1)(k+2)} (indices mod 3)
+    int slot;
+    double sg;
+    if (nu == 3) { slot = mu; sg = -1.0; }
+    else { const int k = 3 - mu - nu; slot = 3 + k; sg = (nu == (mu + 1) % 3) ? 1.0 : -1.0; }
+    cx<double>* out = EB + ((size_t)s * 6 + slot) * 9;
+    for (int e = 0; e < 9; ++e) out[e] = mk(sg * (double)f.e[e].re, sg * (double)f.e[e].im);
   }
   double tot = block_sum<K1_THREADS>(retr, sh);
-  if (threadIdx.x == 0) plaq_part[blockIdx.x] = tot;
+  if (threadIdx.x == 0) plaq_part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
 // Sum the per-block plaquette partials in a fixed order; derive u0 and the stored scalars.
@@ -418,8 +414,9 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
   int nb2 = grid_for(g.V, K2_THREADS);
   WOut o{W->W64 ? (cx<double>*)W->W64 : W64tmp, (cx<float>*)W->W32, (cx<dd>*)W->Wdf, (cx<__half>*)W->W16};
   const bool any_w = o.W64 || o.W32 || o.Wdf || o.W16;  // (a handle for the on-the-fly apply stores none)
-  // A native FP64 copy (kept, or read by the tensor-core build) is computed in FP64; otherwise W is
-  // computed in double-float on the FP32 pipes, from double-float copies of the links and fields.
+  // A native FP64 copy (kept, or read by the tensor-core build) is computed in FP64; otherwise the
+  // clover fields and W are computed in double-float on the FP32 pipes, from double-float copies of
+  // the links and fields.
   const bool fp64 = o.W64 != nullptr;
   cx<dd>* ldd = nullptr;
   cx<dd>* ebdd = nullptr;
@@ -438,14 +435,20 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
   }
   {
     TraceScope ts("clover", st);
-    // (in FP64 always: in double-float it took as long, 2.2 ms at 16^3 x 32; it is bound by the
-    // latency of its link gathers at 8 warps per SM, not by the FP64 pipe)
-    clover_kernel<double><<<nb1, K1_THREADS, 0, st>>>(CanonInputs<LT>{U, EB}, g, EB, part);
+    // with the W formulas in double-float, the clover fields too (1.48 ms against 2.06 ms in FP64 at
+    // 16^3 x 32); the plaquette of either is summed in FP64
+    if (ldd) {
+      to_dd_kernel<LT><<<grid_for(36LL * g.V, 256), 256, 0, st>>>(U, ldd, 36LL * g.V);
+      count_launch();
+      clover_kernel<dd><<<dim3(nb1, 6), K1_THREADS, 0, st>>>(DDInputs{ldd, nullptr}, g, EB, part);
+    } else {
+      clover_kernel<double><<<dim3(nb1, 6), K1_THREADS, 0, st>>>(CanonInputs<LT>{U, EB}, g, EB, part);
+    }
   }
   count_launch();
   {
     TraceScope ts("plaquette_u0", st);
-    scalars_kernel<<<1, 256, 0, st>>>(part, nb1, g, *c, dsc);
+    scalars_kernel<<<1, 256, 0, st>>>(part, 6 * nb1, g, *c, dsc);
   }
   count_launch();
   if (any_w) {
@@ -457,9 +460,7 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
         count_launch();
       }
     } else {
-      to_dd_kernel<LT><<<grid_for(36LL * g.V, 256), 256, 0, st>>>(U, ldd, 36LL * g.V);
       to_dd_kernel<double><<<grid_for(54LL * g.V, 256), 256, 0, st>>>(EB, ebdd, 54LL * g.V);
-      count_launch();
       count_launch();
       const DDInputs in{ldd, ebdd};
       for (int part_id = 0; part_id < 5; ++part_id) {
@@ -615,7 +616,7 @@ int precompute(const ok_lattice* lat, const void* links, ok_prec links_prec, con
   int nb1 = grid_for(g.V, K1_THREADS);
   e = cudaMallocAsync((void**)&EB, (size_t)g.V * 6 * 9 * sizeof(cx<double>), st);
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
-  e = cudaMallocAsync((void**)&part, (size_t)nb1 * sizeof(double), st);
+  e = cudaMallocAsync((void**)&part, (size_t)6 * nb1 * sizeof(double), st);
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
   e = cudaMallocAsync((void**)&dsc, sizeof(WScalars), st);
   if (e != cudaSuccess) { set_cuda_error(e); return fail(OK_ENOMEM); }
