@@ -61,7 +61,9 @@ typedef enum { OK_F64 = 0, OK_F32 = 1, OK_F32_W16 = 2, OK_F16_TC = 3, OK_F32_OTF
 /* Which stored copies a W handle carries (bit mask for ok_precompute_W).  OK_W_DF64 keeps FP64
  * accuracy as double-float pairs (hi + lo, two floats, about 48 significand bits): FP64 applications
  * and residuals on such a handle run on the FP32 pipes, which GB300 executes 58 times faster than its
- * FP64 pipe, with errors of about 1e-14 relative; it takes twice the memory of OK_W_F64.  When a
+ * FP64 pipe, with errors of about 1e-14 relative; it takes twice the memory of OK_W_F64.  Without
+ * OK_W_F64 (and OK_W_F16_TC) in the mask, the clover fields and W themselves are computed in
+ * double-float arithmetic on the FP32 pipes (about 1e-13 relative) instead of FP64.  When a
  * handle has both, ok_apply_M with OK_F64 uses the native OK_W_F64 copy (FP64 rounding exactly),
  * and the true residuals (ok_true_residual and those inside the solvers) use the double-float copy,
  * the faster of the two on GB300. */

@@ -235,9 +235,7 @@ __global__ void __launch_bounds__(K2_THREADS) w_kernel(In in, Geom g, ok_coeffs 
   }
   if (part >= 1 && part <= 3) {
     const int i = part - 1;
-    M3<R> q[8];
-    wform::spatial<R>(in, p, g, s, i, c, u0, q);
-    for (int k = 0; k < 8; ++k) store_mat(o, s, M_WP + 8 * i + k, q[k]);
+    wform::spatial_to<R>(in, p, g, s, i, c, u0, [&](int k, const M3<R>& m) { store_mat(o, s, M_WP + 8 * i + k, m); });
     return;
   }
   // part 4: two-hop colour matrices

@@ -95,12 +95,13 @@ __device__ __forceinline__ void temporal(const A& a, const Site& p, const Geom& 
   t[2] = m_add(tk[0], m_scale(I, tk[1]));
 }
 
-// W^+_i = [[D, S], [S, D]] for spatial direction i: q[sg * 4 + j] are the stored blocks
-// M_WP + 8 i + 4 sg + j, the 2x2 spin blocks (00, 01, 10, 11) of (D +- S) / 2.
+// W^+_i = [[D, S], [S, D]] for spatial direction i: put(sg * 4 + j, block) receives the stored
+// blocks M_WP + 8 i + 4 sg + j, the 2x2 spin blocks (00, 01, 10, 11) of (D +- S) / 2, as they are
+// formed (a caller that stores them keeps no array of them).
 //   S = 1 (x) b0 + sum_l sigma_l (x) b_l,  D = 1 (x) a0 + sum_l sigma_l (x) a_l.
-template <typename R, class A>
-__device__ __forceinline__ void spatial(const A& a, const Site& p, const Geom& g, int s, int i, const ok_coeffs& c,
-                                        double u0, M3<R> (&q)[8]) {
+template <typename R, class A, class Put>
+__device__ __forceinline__ void spatial_to(const A& a, const Site& p, const Geom& g, int s, int i, const ok_coeffs& c,
+                                           double u0, Put&& put) {
   const double u04 = u0 * u0 * u0 * u0;
   const cx<R> I = mk<R>(0, 1);
   const M3<R> Ui = a.U(s, i);
@@ -144,11 +145,17 @@ __device__ __forceinline__ void spatial(const A& a, const Site& p, const Geom& g
   for (int sg = 0; sg < 2; ++sg) {
     M3<R> w[4];
     for (int k = 0; k < 4; ++k) w[k] = m_rscale((R)0.5, sg == 0 ? m_add(av[k], b[k]) : m_sub(av[k], b[k]));
-    q[4 * sg + 0] = m_add(w[0], w[3]);
-    q[4 * sg + 1] = m_sub(w[1], m_scale(I, w[2]));
-    q[4 * sg + 2] = m_add(w[1], m_scale(I, w[2]));
-    q[4 * sg + 3] = m_sub(w[0], w[3]);
+    put(4 * sg + 0, m_add(w[0], w[3]));
+    put(4 * sg + 1, m_sub(w[1], m_scale(I, w[2])));
+    put(4 * sg + 2, m_add(w[1], m_scale(I, w[2])));
+    put(4 * sg + 3, m_sub(w[0], w[3]));
   }
+}
+// The same into an array q[8].
+template <typename R, class A>
+__device__ __forceinline__ void spatial(const A& a, const Site& p, const Geom& g, int s, int i, const ok_coeffs& c,
+                                        double u0, M3<R> (&q)[8]) {
+  spatial_to<R>(a, p, g, s, i, c, u0, [&](int k, const M3<R>& m) { q[k] = m; });
 }
 
 // W^{++}_ii: the colour matrix V = U_i(x) U_i(x+i) (stored M_VII + i).
