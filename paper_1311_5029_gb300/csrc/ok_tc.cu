@@ -530,6 +530,8 @@ __device__ __forceinline__ void multi_finish(double (*bsum)[3], const bool* live
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// Launch bounds: blocks per SM (4: 128 registers, 16 warps); L2 bulk prefetch of the next site's
+// record on (1) or off (0).
 #ifndef OK_TC_MINB
 #define OK_TC_MINB 4
 #endif
