@@ -98,6 +98,7 @@ __global__ void to_dd_kernel(const cx<T>* __restrict__ in, cx<dd>* __restrict__ 
   out[i] = mk(dd((double)v.re), dd((double)v.im));
 }
 
+
 // ---------------------------------------------------------------------------- K1: clover + plaquette
 // F_{mu nu} = (Q - Q^dagger) / 8 with Q the four plaquette leaves around x traversed mu-then-nu;
 // E_i = F_{t i}, B_i = eps_ijk F_jk / 2.  The plaquette leaf U_mu(x) U_nu(x+mu) U_mu^dag(x+nu)
@@ -109,8 +110,8 @@ constexpr int K1_THREADS = 128;
 // field is stored in FP64 in its E or B slot, and the plaquette leaf summed in FP64 into the
 // partial of block (blockIdx.y, blockIdx.x).
 template <typename R, class In>
-__global__ void __launch_bounds__(K1_THREADS) clover_kernel(In in, Geom g, cx<double>* __restrict__ EB,
-                                                            double* __restrict__ plaq_part) {
+__device__ __forceinline__ void clover_body(const In& in, const Geom& g, cx<double>* __restrict__ EB,
+                                            double* __restrict__ plaq_part) {
   __shared__ double sh[K1_THREADS / 32];
   const int s = blockIdx.x * K1_THREADS + threadIdx.x;
   const int pl = blockIdx.y;
@@ -145,6 +146,17 @@ __global__ void __launch_bounds__(K1_THREADS) clover_kernel(In in, Geom g, cx<do
   }
   double tot = block_sum<K1_THREADS>(retr, sh);
   if (threadIdx.x == 0) plaq_part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+}
+// FP64, and double-float at 4 blocks per SM (128 registers: 1.38 ms against 1.54 ms at the
+// compiler's 168 registers, 16^3 x 32).
+template <class In>
+__global__ void __launch_bounds__(K1_THREADS) clover_kernel(In in, Geom g, cx<double>* __restrict__ EB,
+                                                            double* __restrict__ plaq_part) {
+  clover_body<double>(in, g, EB, plaq_part);
+}
+__global__ void __launch_bounds__(K1_THREADS, 4) clover_kernel_dd(DDInputs in, Geom g, cx<double>* __restrict__ EB,
+                                                                  double* __restrict__ plaq_part) {
+  clover_body<dd>(in, g, EB, plaq_part);
 }
 
 // Sum the per-block plaquette partials in a fixed order; derive u0 and the stored scalars.
@@ -215,8 +227,8 @@ constexpr int K2_THREADS = 64;
 // part 0: W^0 and W^+_4; parts 1..3: W^+_i for i = part - 1; part 4: W^{++}_ii, W^{++}_ij, W^{+-}_ij
 // (the formulas of ok_wform.cuh, in precision R: FP64 from CanonInputs, double-float from DDInputs).
 template <typename R, class In>
-__global__ void __launch_bounds__(K2_THREADS) w_kernel(In in, Geom g, ok_coeffs c, const WScalars* __restrict__ scp,
-                                                       WOut o, int part) {
+__device__ __forceinline__ void w_body(const In& in, const Geom& g, const ok_coeffs& c, const WScalars* __restrict__ scp,
+                                       const WOut& o, int part) {
   int s = blockIdx.x * K2_THREADS + threadIdx.x;
   if (s >= g.V) return;
   const double u0 = scp->u0;
@@ -250,6 +262,17 @@ __global__ void __launch_bounds__(K2_THREADS) w_kernel(In in, Geom g, ok_coeffs 
       store_mat(o, s, M_XIJ + pr, x);
     }
   }
+}
+// FP64, and double-float at 8 blocks per SM (128 registers: 2.14 ms against 2.46 ms per step at
+// the compiler's 168 registers, 16^3 x 32).
+template <class In>
+__global__ void __launch_bounds__(K2_THREADS) w_kernel(In in, Geom g, ok_coeffs c, const WScalars* __restrict__ scp,
+                                                       WOut o, int part) {
+  w_body<double>(in, g, c, scp, o, part);
+}
+__global__ void __launch_bounds__(K2_THREADS, 8) w_kernel_dd(DDInputs in, Geom g, ok_coeffs c,
+                                                             const WScalars* __restrict__ scp, WOut o, int part) {
+  w_body<dd>(in, g, c, scp, o, part);
 }
 
 // ---------------------------------------------------------------------------- expand (inspection)
@@ -438,9 +461,9 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
     if (ldd) {
       to_dd_kernel<LT><<<grid_for(36LL * g.V, 256), 256, 0, st>>>(U, ldd, 36LL * g.V);
       count_launch();
-      clover_kernel<dd><<<dim3(nb1, 6), K1_THREADS, 0, st>>>(DDInputs{ldd, nullptr}, g, EB, part);
+      clover_kernel_dd<<<dim3(nb1, 6), K1_THREADS, 0, st>>>(DDInputs{ldd, nullptr}, g, EB, part);
     } else {
-      clover_kernel<double><<<dim3(nb1, 6), K1_THREADS, 0, st>>>(CanonInputs<LT>{U, EB}, g, EB, part);
+      clover_kernel<<<dim3(nb1, 6), K1_THREADS, 0, st>>>(CanonInputs<LT>{U, EB}, g, EB, part);
     }
   }
   count_launch();
@@ -454,7 +477,7 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
     if (fp64) {
       const CanonInputs<LT> in{U, EB};
       for (int part_id = 0; part_id < 5; ++part_id) {
-        w_kernel<double><<<nb2, K2_THREADS, 0, st>>>(in, g, *c, dsc, o, part_id);
+        w_kernel<<<nb2, K2_THREADS, 0, st>>>(in, g, *c, dsc, o, part_id);
         count_launch();
       }
     } else {
@@ -462,7 +485,7 @@ static int run_precompute(ok_W* W, const void* links, const ok_coeffs* c, cudaSt
       count_launch();
       const DDInputs in{ldd, ebdd};
       for (int part_id = 0; part_id < 5; ++part_id) {
-        w_kernel<dd><<<nb2, K2_THREADS, 0, st>>>(in, g, *c, dsc, o, part_id);
+        w_kernel_dd<<<nb2, K2_THREADS, 0, st>>>(in, g, *c, dsc, o, part_id);
         count_launch();
       }
     }
