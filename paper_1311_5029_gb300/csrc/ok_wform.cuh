@@ -1,8 +1,8 @@
 // The forward W matrices of one site (Sec. 2.2, Eqs. shifted_W_first .. shifted_W_last) in the
 // stored representation of ok_precompute.cu, computed in precision R from the links and the
-// clover fields E_k, B_k.  Two users: the precompute (R = double; every matrix is stored) and the
-// on-the-fly apply (R = float; each group of matrices is built where a hop needs it and used at
-// once).  The accessor A provides the inputs:
+// clover fields E_k, B_k.  Two users: the precompute (R = double, or the double-float dd on the FP32
+// pipes; every matrix is stored) and the on-the-fly apply (R = float; each group of matrices is
+// built where a hop needs it and used at once).  The accessor A provides the inputs:
 //   M3<R> A::U(int site, int mu)   the link U_mu(site)
 //   M3<R> A::F(int site, int k)    E_k(site) for k = 0, 1, 2 and B_{k-3}(site) for k = 3, 4, 5
 // Gauge fields are periodic, so neighbour sites wrap without a sign.
