@@ -68,3 +68,26 @@ def test_binding_rejects_host_tensors(lib):
     torch = pytest.importorskip("torch")
     with pytest.raises(ValueError):
         ok.precompute_W(torch.zeros((2, 2, 2, 2, 4, 3, 3), dtype=torch.complex128), {})
+
+
+def test_binding_constants_match_the_header():
+    """The binding's precision, copy, solve-mode and reduction constants are the header's values."""
+    import re
+    text = open(ok.HEADER).read()
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(OK_\w+)\s+(\d+)\b", text)}
+    enum = re.search(r"typedef enum \{([^}]*)\} ok_prec;", text).group(1)
+    defines.update({m.group(1): int(m.group(2)) for m in re.finditer(r"(OK_\w+)\s*=\s*(\d+)", enum)})
+    pairs = {"F64": "OK_F64", "F32": "OK_F32", "F32_W16": "OK_F32_W16", "F16_TC": "OK_F16_TC", "F32_OTF": "OK_F32_OTF",
+             "W_F64": "OK_W_F64", "W_F32": "OK_W_F32", "W_DF64": "OK_W_DF64", "W_F16": "OK_W_F16",
+             "W_LINKS": "OK_W_LINKS", "W_F16_TC": "OK_W_F16_TC", "W_OTF": "OK_W_OTF",
+             "SOLVE_AUTO": "OK_SOLVE_AUTO", "SOLVE_F64": "OK_SOLVE_F64", "SOLVE_MIXED": "OK_SOLVE_MIXED",
+             "SOLVE_MIXED16": "OK_SOLVE_MIXED16", "SOLVE_MIXED_TC": "OK_SOLVE_MIXED_TC", "SOLVE_DEFECT": "OK_SOLVE_DEFECT",
+             "REDUCE_DOT": "OK_REDUCE_DOT", "REDUCE_TS": "OK_REDUCE_TS"}
+    for py, c in pairs.items():
+        assert c in defines, c
+        assert getattr(ok, py) == defines[c], (py, getattr(ok, py), defines[c])
+    # the copy flags are distinct bits; the defect flag is a bit above every solve mode
+    flags = [defines[c] for c in pairs.values() if c.startswith("OK_W_")]
+    assert all(f & (f - 1) == 0 for f in flags) and len(set(flags)) == len(flags)
+    modes = [defines[c] for c in ("OK_SOLVE_AUTO", "OK_SOLVE_F64", "OK_SOLVE_MIXED", "OK_SOLVE_MIXED16", "OK_SOLVE_MIXED_TC")]
+    assert all(m & defines["OK_SOLVE_DEFECT"] == 0 for m in modes)
